@@ -1,0 +1,150 @@
+"""Seeded synthetic point clouds and ROI lists.
+
+This module only draws inputs: it holds none of the density-estimation
+arithmetic, imports nothing from the CUDA binding, and is the one module that
+both the CUDA path's callers and the oracle's callers share.
+
+Clouds follow the shape of the paper's cosmological data (Sec. 3.3: a dense
+central cluster with sub-clusters, and filaments) at sizes the paper did not
+reach:
+
+* ``plain_cloud``      50% uniform + 50% from 8 isotropic Gaussian clusters
+* ``soneira_peebles``  hierarchical clustering (eta sub-spheres per level,
+                       radius ratio lambda), points at the deepest centres
+* ``cosmology_cloud``  80% Soneira-Peebles + 20% uniform background in a
+                       periodic unit box (coordinates wrapped into [0, 1))
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 260120758
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def _wrap01(x: np.ndarray) -> np.ndarray:
+    """Wrap float64 coordinates into [0, 1) and round to float32 inside [0, 1)."""
+    x = x - np.floor(x)
+    f = x.astype(np.float32)
+    f[f >= np.float32(1.0)] = np.float32(0.0)
+    return f
+
+
+def uniform_cloud(n: int, seed: int, lo=0.0, hi=1.0) -> np.ndarray:
+    """n float32 points uniform in [lo, hi)^3."""
+    r = _rng(seed)
+    return (lo + (hi - lo) * r.random((n, 3))).astype(np.float32)
+
+
+def plain_cloud(n: int = 100_000, seed: int = SEED_BASE + 1, n_clusters: int = 8,
+                sigma: float = 0.02) -> np.ndarray:
+    """Half uniform in the unit cube, half split evenly over isotropic Gaussians.
+
+    Cluster centres are uniform in [0.1, 0.9]^3; samples falling outside
+    [0, 1)^3 are redrawn.
+    """
+    r = _rng(seed)
+    n_uni = n // 2
+    n_cl = n - n_uni
+    uni = r.random((n_uni, 3))
+    centres = 0.1 + 0.8 * r.random((n_clusters, 3))
+    per = np.full(n_clusters, n_cl // n_clusters)
+    per[: n_cl - per.sum()] += 1
+    parts = [uni]
+    for c, m in zip(centres, per):
+        got = np.empty((0, 3))
+        while got.shape[0] < m:
+            s = c + sigma * r.standard_normal((2 * (m - got.shape[0]) + 8, 3))
+            ok = np.all((s >= 0.0) & (s < 1.0), axis=1)
+            got = np.concatenate([got, s[ok]])
+        parts.append(got[:m])
+    pts = np.concatenate(parts).astype(np.float32)
+    pts[pts >= np.float32(1.0)] = np.nextafter(np.float32(1.0), np.float32(0.0))
+    return pts
+
+
+def _ball(r: np.random.Generator, m: int) -> np.ndarray:
+    """m points uniform in the unit ball."""
+    d = r.standard_normal((m, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return d * np.cbrt(r.random((m, 1)))
+
+
+def soneira_peebles(count: int, seed: int, eta: int = 4, lam: float = 1.9, levels: int = 12,
+                    radius: float = 0.25) -> np.ndarray:
+    """Soneira-Peebles clustering, float64, not wrapped.
+
+    A top-level sphere of the given radius has eta sub-spheres of radius
+    r / lam placed uniformly inside it, recursively; after ``levels`` levels
+    the points are the centres of the deepest spheres (eta^(levels-1) per top
+    sphere). Top spheres are centred uniformly in the unit cube and added
+    until at least ``count`` points exist; a seeded subset of ``count`` of them
+    is returned.
+    """
+    r = _rng(seed)
+    per_top = eta ** (levels - 1)
+    n_top = max(1, -(-count // per_top))
+    out = []
+    for _ in range(n_top):
+        c = r.random((1, 3))
+        rad = radius
+        for _lvl in range(1, levels):
+            c = np.repeat(c, eta, axis=0) + rad * _ball(r, c.shape[0] * eta)
+            rad = rad / lam
+        out.append(c)
+    pts = np.concatenate(out)
+    if pts.shape[0] > count:
+        keep = np.sort(r.choice(pts.shape[0], size=count, replace=False))
+        pts = pts[keep]
+    return pts
+
+
+def cosmology_cloud(n: int = 16_777_216, seed: int = SEED_BASE + 2, background: float = 0.2,
+                    levels: int = 12) -> np.ndarray:
+    """(1 - background) Soneira-Peebles + background uniform, wrapped into [0, 1)^3."""
+    r = _rng(seed)
+    n_bg = int(round(background * n))
+    n_sp = n - n_bg
+    sp = soneira_peebles(n_sp, seed + 7, levels=levels)
+    bg = r.random((n_bg, 3))
+    pts = np.concatenate([sp, bg])
+    perm = r.permutation(n)
+    return _wrap01(pts[perm])
+
+
+def densest_cell_centre(xyz: np.ndarray, cells: int = 256) -> np.ndarray:
+    """Centre of the most populated cell of a cells^3 histogram over [0, 1)^3."""
+    q = np.clip((np.asarray(xyz, dtype=np.float64) * cells).astype(np.int64), 0, cells - 1)
+    key = (q[:, 2] * cells + q[:, 1]) * cells + q[:, 0]
+    cnt = np.bincount(key, minlength=cells ** 3)
+    best = int(np.argmax(cnt))
+    ix, iy, iz = best % cells, (best // cells) % cells, best // (cells * cells)
+    return (np.array([ix, iy, iz], dtype=np.float64) + 0.5) / cells
+
+
+def nested_rois(centre, n_roi: int = 5, shrink: float = 4.0):
+    """Cubic ROIs of edge shrink^-i (i = 0..n_roi-1) centred on ``centre``,
+    shifted to stay inside the unit cube. Returns [(lo[3], hi[3]), ...] in float64."""
+    c = np.asarray(centre, dtype=np.float64)
+    rois = []
+    for i in range(n_roi):
+        e = shrink ** (-i)
+        lo = np.clip(c - e / 2, 0.0, 1.0 - e)
+        rois.append((lo.copy(), lo + e))
+    return rois
+
+
+def lattice_cloud(m: int, spacing: float, origin=0.0) -> np.ndarray:
+    """m^3 points on a cubic lattice, x fastest."""
+    g = origin + spacing * np.arange(m, dtype=np.float64)
+    zz, yy, xx = np.meshgrid(g, g, g, indexing="ij")
+    return np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1).astype(np.float32)
+
+
+def random_densities(n: int, seed: int) -> np.ndarray:
+    """Positive float32 values spread over several decades (selection inputs)."""
+    r = _rng(seed)
+    return np.exp(r.normal(0.0, 3.0, n)).astype(np.float32)

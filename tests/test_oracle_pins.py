@@ -1,0 +1,295 @@
+"""Pins for the FP64 oracle: closed forms, invariants, hand-derived values and a
+second, sort-based route on tiny inputs. CPU only.
+
+Each test names the plausible oracle mistake it would catch.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_20758_gb300 import synth
+
+
+def _load(golden_dir, name):
+    with open(os.path.join(golden_dir, name)) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------------------
+# Normalisation constants
+# --------------------------------------------------------------------------
+def test_p3_matches_chi2_cdf():
+    """Truncated-Gaussian renormaliser = P(chi^2_3 <= 9), via scipy's chi2 (independent route)."""
+    stats = pytest.importorskip("scipy.stats")
+    assert abs(oracle.P3 - stats.chi2.cdf(9.0, 3)) < 1e-14
+
+
+@pytest.mark.parametrize("kernel,ell,tol", [
+    (oracle.GAUSS3, (0.1, 0.1, 0.1), 1e-3),       # catches a wrong (2 pi)^1.5, h^3 or a missing P3 (0.971)
+    (oracle.EPAN, (0.30, 0.20, 0.25), 2e-3),      # catches a wrong 15/(8 pi) or l_x l_y l_z
+])
+def test_single_particle_riemann_mass(kernel, ell, tol):
+    """Riemann sum of one interior particle's kernel over the grid ~= 1 (Eq. 7 normalisation)."""
+    xyz = np.array([[0.5, 0.5, 0.5]], dtype=np.float32)
+    box = ((0, 0, 0), (1, 1, 1))
+    dims = (81, 81, 81)
+    out = oracle.kde_grid(xyz, np.array([ell]), box, dims, kernel, oracle.SCOPE_GLOBAL)
+    m = oracle.grid_mass(out["rho"], box, dims)
+    assert abs(m - 1.0) < tol, m
+
+
+def test_epan_nodes_golden(golden_dir):
+    """Hand-derived node values: peak 15/(8 pi N l_x l_y l_z) and per-axis fall-off.
+    Catches transposed axes, a wrong normaliser and the x-fastest layout."""
+    g = _load(golden_dir, "epan_nodes.json")
+    xyz = np.array(g["points"], dtype=np.float32)
+    ell = np.tile(np.array(g["ell"], dtype=np.float64), (xyz.shape[0], 1))
+    dims = g["dims"]
+    out = oracle.kde_grid(xyz, ell, g["box"], dims, oracle.EPAN, oracle.SCOPE_GLOBAL)
+    peak = 0.25 * 15.0 / (8.0 * math.pi * 0.3 * 0.5 * 0.4)
+    expect = {
+        (2, 2, 2): peak,
+        (3, 2, 2): peak * (1 - (0.25 / 0.3) ** 2),
+        (2, 3, 2): peak * (1 - (0.25 / 0.5) ** 2),
+        (2, 2, 3): peak * (1 - (0.25 / 0.4) ** 2),
+        (4, 2, 2): 0.0,
+    }
+    for node in g["nodes"]:
+        i, j, k = node["ijk"]
+        v = out["rho"][i + j * dims[0] + k * dims[0] * dims[1]]
+        assert v == pytest.approx(expect[(i, j, k)], rel=1e-13, abs=1e-300)
+
+
+def test_index_layout_argmax():
+    """One off-centre particle: the maximum sits at flat index i_x + i_y*nx + i_z*nx*ny."""
+    dims = (9, 7, 5)
+    box = ((0, 0, 0), (8, 6, 4))            # s = 1 on every axis
+    xyz = np.array([[6.0, 2.0, 1.0]], dtype=np.float32)
+    out = oracle.kde_grid(xyz, np.array([[1.5, 1.5, 1.5]]), box, dims, oracle.EPAN,
+                          oracle.SCOPE_GLOBAL)
+    assert int(np.argmax(out["rho"])) == 6 + 2 * 9 + 1 * 9 * 7
+
+
+@pytest.mark.parametrize("kernel,R", [(oracle.EPAN, 3.5), (oracle.GAUSS3, 1.5)])
+def test_lattice_sum_integer_enumeration(kernel, R):
+    """Interior node of a cubic lattice (spacing a), fixed bandwidth R*a: the density equals
+    (1/N) * C/(R a)^3 * sum over integer vectors m in support of the kernel profile,
+    enumerated here with integer loops (independent of the oracle's pair loop)."""
+    m = 17
+    a = 1.0 / 16
+    xyz = synth.lattice_cloud(m, a)
+    n = xyz.shape[0]
+    ell = np.full((n, 3), R * a)
+    box = ((0, 0, 0), (1, 1, 1))
+    node = np.array([[8 * a, 8 * a, 8 * a]])
+    rho = oracle.density_at(xyz, ell, node, kernel, 1.0 / n)["rho"][0]
+    r = int(math.ceil(3 * R)) + 1
+    acc = 0.0
+    for i, j, k in itertools.product(range(-r, r + 1), repeat=3):
+        q2 = (i * i + j * j + k * k) / (R * R)
+        if kernel == oracle.EPAN and q2 < 1:
+            acc += 1 - q2
+        if kernel == oracle.GAUSS3 and q2 < 9:
+            acc += math.exp(-q2 / 2)
+    c = 15 / (8 * math.pi) if kernel == oracle.EPAN else 1 / ((2 * math.pi) ** 1.5 * oracle.P3)
+    expect = acc * c / (R * a) ** 3 / n
+    assert rho == pytest.approx(expect, rel=1e-12)
+    # and the lattice density is the continuum value 1/(N a^3) up to the lattice-sum error
+    assert rho * n * a ** 3 == pytest.approx(1.0, rel=0.05)
+
+
+def test_scale_invariance_power_of_two():
+    """Coordinates and box times 2^3: kNN h times 8 and densities times 2^-9, bit for bit.
+    Catches a wrong power of h in the normaliser or a mis-scaled node position."""
+    xyz = synth.plain_cloud(1500, seed=5)
+    box = ((0.1, 0.05, 0.0), (0.9, 1.0, 0.8))
+    dims = (9, 8, 7)
+    h, _, _ = oracle.knn(xyz, 8)
+    xyz8 = xyz * np.float32(8)
+    h8, _, _ = oracle.knn(xyz8, 8)
+    assert np.array_equal(h8, h * np.float32(8))
+    box8 = tuple(tuple(8 * v for v in b) for b in box)
+    for kernel in (oracle.EPAN, oracle.GAUSS3):
+        g = oracle.kde_grid(xyz, oracle.iso_ell(h), box, dims, kernel, oracle.SCOPE_GLOBAL)
+        g8 = oracle.kde_grid(xyz8, oracle.iso_ell(h8), box8, dims, kernel, oracle.SCOPE_GLOBAL)
+        assert np.array_equal(g8["rho"], g["rho"] * 2.0 ** -9)
+
+
+def test_permutation_invariance():
+    """Reordering the particles changes nothing beyond summation order.
+    Catches any dependence on j's position other than the documented tie-break."""
+    xyz = synth.plain_cloud(1200, seed=9)
+    perm = np.random.default_rng(3).permutation(xyz.shape[0])
+    h, nbr, _ = oracle.knn(xyz, 6, want_neighbours=True)
+    hp, nbrp, _ = oracle.knn(xyz[perm], 6, want_neighbours=True)
+    assert np.array_equal(hp, h[perm])
+    # neighbour sets map through the permutation (no ties in a random cloud)
+    for t in range(0, xyz.shape[0], 37):
+        assert set(perm[nbrp[t]]) == set(nbr[perm[t]])
+    box = ((0, 0, 0), (1, 1, 1))
+    g = oracle.kde_grid(xyz, oracle.iso_ell(h), box, (6, 6, 6), oracle.GAUSS3, oracle.SCOPE_GLOBAL)
+    gp = oracle.kde_grid(xyz[perm], oracle.iso_ell(hp), box, (6, 6, 6), oracle.GAUSS3,
+                         oracle.SCOPE_GLOBAL)
+    np.testing.assert_allclose(gp["rho"], g["rho"], rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# kNN
+# --------------------------------------------------------------------------
+def test_knn_golden(golden_dir):
+    """Hand-derived neighbours and bandwidths, including an exact distance tie."""
+    g = _load(golden_dir, "knn_line.json")
+    for case in g["cases"]:
+        xyz = np.array(case["points"], dtype=np.float32)
+        h, nbr, _ = oracle.knn(xyz, case["k"], want_neighbours=True)
+        assert np.array_equal(h, np.array([np.float32(float(v)) for v in case["h"]]))
+        assert nbr.tolist() == case["neighbours"]
+
+
+def _knn_by_sort(xyz, k):
+    """Second route: full FP64 distance matrix, lexicographic sort by (d2, j)."""
+    a = xyz.astype(np.float64)
+    n = a.shape[0]
+    d = a[:, None, :] - a[None, :, :]
+    d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+    h = np.empty(n, dtype=np.float32)
+    nb = np.empty((n, k), dtype=np.int64)
+    j = np.arange(n)
+    for i in range(n):
+        order = np.lexsort((j, d2[i]))
+        order = order[order != i][:k]
+        nb[i] = order
+        h[i] = np.float32(math.sqrt(d2[i, order[-1]]))
+    return h, nb
+
+
+@pytest.mark.parametrize("k", [1, 5, 32])
+def test_knn_matches_sort_route_with_ties(k):
+    """Insertion-based top-k vs a full sort, on a cloud with duplicates and lattice ties."""
+    a = synth.plain_cloud(400, seed=11)
+    lat = synth.lattice_cloud(5, 0.125, origin=0.25)
+    dup = a[:40].copy()
+    xyz = np.concatenate([a, lat, dup])
+    h, nbr, _ = oracle.knn(xyz, k, want_neighbours=True)
+    h2, nb2 = _knn_by_sort(xyz, k)
+    assert np.array_equal(h, h2)
+    assert np.array_equal(nbr, nb2)
+
+
+def test_knn_rejects_degenerate():
+    with pytest.raises(ValueError):
+        oracle.knn(np.zeros((4, 3), np.float32), 4)
+
+
+# --------------------------------------------------------------------------
+# Modified Breiman estimator pieces
+# --------------------------------------------------------------------------
+def test_mbe_ell_golden(golden_dir):
+    g = _load(golden_dir, "mbe_ell.json")
+    v = np.array(g["values"], dtype=np.float64)
+    assert oracle.percentile_linear(v, 20) == pytest.approx(float(g["p20"]), rel=1e-15)
+    assert oracle.percentile_linear(v, 80) == pytest.approx(float(g["p80"]), rel=1e-15)
+    pts = np.stack([v, v, v], axis=1)
+    ell = oracle.mbe_initial_ell(pts)
+    assert ell == pytest.approx([float(g["ell_value"])] * 3, rel=1e-14)
+
+
+def test_percentile_matches_numpy():
+    """Special case that reduces to a library routine: numpy's 'linear' percentile."""
+    r = np.random.default_rng(1)
+    for n in (2, 3, 10, 101, 1000):
+        v = r.random(n) * 10 - 3
+        for q in (0, 20, 33.3, 80, 100):
+            assert oracle.percentile_linear(v, q) == pytest.approx(
+                np.percentile(v, q, method="linear"), rel=1e-14, abs=1e-14)
+
+
+def test_trilinear_reproduces_linear_fields():
+    """Trilinear interpolation is exact for f = a + b x + c y + d z (catches swapped weights)."""
+    box = ((0.2, -1.0, 0.5), (1.4, 2.0, 0.9))
+    dims = (5, 7, 4)
+    nodes = oracle.grid_nodes(box, dims)
+    f = lambda p: 0.3 + 1.7 * p[:, 0] - 2.1 * p[:, 1] + 0.9 * p[:, 2]
+    r = np.random.default_rng(2)
+    lo, hi = np.array(box[0]), np.array(box[1])
+    pts = lo + (hi - lo) * r.random((500, 3))
+    pts = np.concatenate([pts, [hi, lo]])
+    np.testing.assert_allclose(oracle.trilinear(f(nodes), box, dims, pts), f(pts),
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_mbe_uniform_lattice_interior():
+    """Uniform data: pilot ~ aveDen in the interior, so l^(j) ~ min(l, 5 s_k);
+    every l^(j) respects the cap (Eq. 6). A 'sum' reading of Eq. 5 would pin all
+    l^(j) at the cap; a missing cube root would move the interior away from l."""
+    xyz = synth.lattice_cloud(16, 1.0 / 15)
+    box = ((0, 0, 0), (1, 1, 1))
+    dims = (9, 9, 9)
+    out = oracle.mbe(xyz, box, dims, kernel=oracle.EPAN)
+    s = out["s"]
+    ell_j = out["ell_j"][out["member"]]
+    assert np.all(ell_j <= 5 * s + 1e-15)
+    ell0 = out["ell0"]
+    # interior particles: ratio aveDen/pDen is within the boundary-deficit range
+    inner = np.all((xyz > 0.3) & (xyz < 0.7), axis=1)[out["member"]]
+    exp_inner = np.minimum(ell0, 5 * s)
+    assert np.all(np.abs(ell_j[inner] / exp_inner - 1) < 0.25)
+    assert not np.all(np.isclose(ell_j, 5 * s))
+
+
+def test_mbe_zero_pilot_gives_cap():
+    """pDen_j = 0 drives l^(j) to the cap 5 s_k (limit of Eq. 6)."""
+    # a tight central clump makes l tiny (Eq. 1), so the nodes around a lone outlier see nothing
+    r = np.random.default_rng(7)
+    clump = (0.5 + 1e-3 * (r.random((100, 3)) - 0.5)).astype(np.float32)
+    a = np.concatenate([clump, np.array([[0.1, 0.1, 0.1], [0.9, 0.15, 0.6]], dtype=np.float32)])
+    box = ((0, 0, 0), (1, 1, 1))
+    out = oracle.mbe(a, box, (5, 5, 5))
+    assert np.all(out["pden"] >= 0)
+    zero = out["pden"] == 0
+    assert zero.sum() == 2 and zero[-2:].all()
+    ell_in = out["ell_j"][out["member"]]
+    np.testing.assert_allclose(ell_in[zero], np.tile(5 * out["s"], (2, 1)))
+    assert np.all(ell_in[~zero] < 5 * out["s"])
+
+
+def test_clip_scope_normalises_by_box_count():
+    """CLIP scope: particles outside B are excluded and N_B normalises (Eq. 7 over B)."""
+    xyz = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 0.55], [5, 5, 5]], dtype=np.float32)
+    ell = np.full((3, 3), 0.2)
+    box = ((0, 0, 0), (1, 1, 1))
+    clip = oracle.kde_grid(xyz, ell, box, (5, 5, 5), oracle.EPAN, oracle.SCOPE_CLIP)
+    glob = oracle.kde_grid(xyz, ell, box, (5, 5, 5), oracle.EPAN, oracle.SCOPE_GLOBAL)
+    assert clip["neff"] == 2
+    np.testing.assert_allclose(clip["rho"] * 2, glob["rho"] * 3, rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Selection
+# --------------------------------------------------------------------------
+def test_select_golden(golden_dir):
+    g = _load(golden_dir, "select_rank.json")
+    for case in g["cases"]:
+        d = np.array(case["density"], dtype=np.float32)
+        ids = np.array(case["ids"], dtype=np.uint32)
+        if "threshold" in case:
+            t, sel = oracle.select(d, ids, threshold=case["threshold"])
+        else:
+            t, sel = oracle.select(d, ids, percentile=case["percentile"])
+        assert float(t) == case["t"]
+        assert sel.tolist() == case["selected"]
+
+
+def test_select_brute_force():
+    """Selection equals a per-element filter with the nearest-rank threshold."""
+    d = synth.random_densities(5000, 4)
+    ids = np.arange(5000, dtype=np.uint32) * 3
+    t, sel = oracle.select(d, ids, percentile=90)
+    assert int(np.sum(d <= t)) >= math.ceil(0.9 * 5000)
+    assert int(np.sum(d < t)) < math.ceil(0.9 * 5000)
+    assert sel.tolist() == [int(i) for i, v in zip(ids, d) if v > t]
