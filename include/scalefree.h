@@ -1,0 +1,228 @@
+/*
+ * scalefree.h -- C ABI of libscalefree.so: on-the-fly adaptive kernel density
+ * estimation over a region of interest (ROI) of a large float32 xyz point
+ * cloud, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one of ScaleFree (arXiv 2601.20758, Sec. 3): a density
+ * field on a uniform grid over a box B (Sec. 3.1), from per-particle adaptive
+ * smoothing lengths, evaluated by gathering the kernel contributions of the
+ * particles near each node (Sec. 3.2.1, Algorithms 1-4), plus density-threshold
+ * selection of points (Sec. 4.1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers named d_* are DEVICE pointers on the current CUDA device; h_* are
+ *   HOST pointers. The caller owns every buffer passed in. The library owns
+ *   the index (sf_index) and its internal workspaces.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream). Calls are stream-ordered. A call that returns a host scalar
+ *   (h_*) synchronises that stream before returning.
+ * - Every call returns an sf_status. Invalid arguments are rejected before
+ *   any launch. sf_last_error() gives a message for the calling thread.
+ * - Float inputs must be finite.
+ * - Coordinates are world coordinates in float32; boxes are closed boxes
+ *   [lo, hi] in double.
+ * - Determinism: results are bit-identical from run to run for the same
+ *   inputs (no floating-point atomics anywhere).
+ * - One index may be used from several host threads on different streams
+ *   once sf_bandwidths has returned; each stream gets its own workspace.
+ */
+#ifndef SCALEFREE_H
+#define SCALEFREE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sf_index sf_index;
+
+typedef enum {
+    SF_OK = 0,
+    SF_ERR_INVALID_ARG = 1, /* NULL pointer, bad size, bad enum, dims < 2 ...      */
+    SF_ERR_OOM = 2,         /* device allocation failed                              */
+    SF_ERR_CUDA = 3,        /* a CUDA call or a kernel launch failed                 */
+    SF_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                    */
+    SF_ERR_DEGENERATE = 5,  /* N <= k, fewer than 2 particles in B, P80 == P20     */
+    SF_ERR_EMPTY_ROI = 6,   /* no particle of the scope lies in the ROI              */
+    SF_ERR_BUSY = 7,        /* not admitted (serving)                                */
+    SF_ERR_CAPACITY = 8     /* an output buffer is smaller than the result           */
+} sf_status;
+
+/* Kernels.
+ * SF_K_EPAN   (Eqs. 4 and 7): K = 15/(8 pi) / (lx ly lz) * (1 - q) for q < 1, else 0.
+ * SF_K_GAUSS3: K = exp(-q/2) / ((2 pi)^(3/2) lx ly lz P3) for q < 9, else 0,
+ *             P3 = P(chi^2_3 <= 9), so that the truncated kernel integrates to 1.
+ * with q = sum_k ((r_k - y_k) / l_k)^2 (Eq. 8). */
+enum { SF_K_EPAN = 0, SF_K_GAUSS3 = 1 };
+
+/* Bandwidth rules.
+ * SF_BW_KNN  : l_j = (h_j, h_j, h_j), h_j = distance to the k-th nearest other
+ *              point, computed once per cloud by sf_bandwidths.
+ * SF_BW_MBE  : the paper's modified Breiman estimator, per ROI (Eqs. 1, 2, 5, 6).
+ * SF_BW_FIXED: l_j = fixed_h for every particle. */
+enum { SF_BW_KNN = 0, SF_BW_MBE = 1, SF_BW_FIXED = 2 };
+
+/* Which particles enter the sum, and the normaliser N_eff.
+ * SF_SCOPE_CLIP  : particles inside the ROI box B, N_eff = N_B (Eq. 2, Sec. 3.1).
+ * SF_SCOPE_GLOBAL: all particles, N_eff = N. */
+enum { SF_SCOPE_CLIP = 0, SF_SCOPE_GLOBAL = 1 };
+
+enum { SF_PREC_FP32 = 0 };
+
+/* Point densities: DIRECT evaluates the kernel sum at each point (self term
+ * included); INTERP interpolates the ROI grid trilinearly (Sec. 3.1, last step). */
+enum { SF_POINTS_DIRECT = 0, SF_POINTS_INTERP = 1 };
+
+typedef struct {
+    double lo[3];
+    double hi[3];
+} sf_box;
+
+/* 80 bytes, fixed layout. */
+typedef struct {
+    int32_t rule;        /* SF_BW_*                                              */
+    int32_t k;           /* kNN neighbours (SF_BW_KNN), 1 <= k <= 256            */
+    double fixed_h[3];   /* SF_BW_FIXED smoothing lengths, > 0                   */
+    double cap_factor;   /* SF_BW_MBE: l^(j) <= cap_factor * s_k (paper: 5)      */
+    double p_lo, p_hi;   /* SF_BW_MBE: percentiles of Eq. 1 (paper: 20, 80)      */
+    double log_base;     /* SF_BW_MBE: base of the log in Eq. 1; <= 0 means e    */
+    int32_t scope;       /* SF_SCOPE_*                                           */
+    int32_t prec;        /* SF_PREC_FP32                                         */
+    int32_t points_mode; /* SF_POINTS_*                                          */
+    int32_t reserved;    /* must be 0                                            */
+} sf_params;
+
+/* Fill *p with the defaults: KNN, k = 32, cap 5, percentiles 20/80, natural
+ * log, GLOBAL scope, FP32, DIRECT points. */
+void sf_params_default(sf_params *p);
+
+/*
+ * sf_build_index -- copy the cloud and build the spatial index on the device.
+ *
+ * Replaces the CPU k-d tree of Sec. 3.2 (built on the CPU and uploaded there)
+ * by a GPU index: points radix-sorted by 63-bit Morton key (21 bits per axis
+ * over the cloud's bounding box), stored as float4 (x, y, z, h) in that
+ * order; leaves are runs of 32 consecutive sorted points and every upper
+ * level groups 32 nodes; each node keeps its bounding box and the largest
+ * smoothing length below it.
+ *
+ * d_xyz : device float32 [n][3] (x, y, z interleaved); read only, not kept.
+ * n     : 1 <= n < 2^31.
+ * out   : receives the new index; free it with sf_free_index.
+ * Synchronises `stream` (the node count is read back). Errors: INVALID_ARG,
+ * OOM, CUDA.
+ */
+sf_status sf_build_index(const float *d_xyz, int64_t n, void *stream, sf_index **out);
+
+/* Number of points in the index. */
+int64_t sf_index_size(const sf_index *idx);
+
+/*
+ * sf_bandwidths -- per-point smoothing lengths that do not depend on the ROI.
+ *
+ * SF_BW_KNN  : h_j = Euclidean distance to the k-th nearest other point of the
+ *              cloud. The neighbour set is exact with respect to FP64 squared
+ *              distances ((dx*dx)+(dy*dy))+(dz*dz) of the float inputs, ties broken
+ *              by the smaller original index, and h_j = (float)sqrt(d2_k) -- it
+ *              is bit-identical to a brute-force FP64 evaluation. n <= k gives
+ *              DEGENERATE.
+ * SF_BW_FIXED: stores fixed_h (isotropic only if the three are equal).
+ * SF_BW_MBE  : nothing to precompute (the rule is per ROI); returns SF_OK.
+ * The result stays resident in the index and is used by later calls with the
+ * same rule.
+ */
+sf_status sf_bandwidths(sf_index *idx, const sf_params *params, void *stream);
+
+/*
+ * sf_get_bandwidths -- copy the kNN bandwidths h_j out, in ORIGINAL point
+ * order. d_h: device float [n]. INVALID_ARG if no kNN bandwidths were built.
+ */
+sf_status sf_get_bandwidths(const sf_index *idx, float *d_h, void *stream);
+
+/*
+ * sf_knn_neighbours -- the k nearest other points of every point (for
+ * verification): d_nbr device uint32 [n][k], original indices, row i for
+ * original point i, in no particular order within a row; d_h device float [n]
+ * (nullable). Same exactness contract as sf_bandwidths; does not change the
+ * resident bandwidths.
+ */
+sf_status sf_knn_neighbours(sf_index *idx, int32_t k, uint32_t *d_nbr, float *d_h, void *stream);
+
+/*
+ * sf_kde_grid -- density at every node of a dims[0] x dims[1] x dims[2] grid
+ * over the ROI box (Sec. 3.1, Eq. 7; Algorithm 4's output).
+ *
+ * Nodes are vertex-centred: r_k(i) = lo_k + i * s_k, s_k = (hi_k - lo_k) /
+ * (dims[k] - 1), so dims[k] >= 2 and hi_k > lo_k. d_out is device float
+ * [dims[2]][dims[1]][dims[0]] (x fastest, index i_x + i_y*dims[0] +
+ * i_z*dims[0]*dims[1], as in Algorithms 2 and 4).
+ * rule KNN needs sf_bandwidths(KNN) first; FIXED uses params->fixed_h; MBE
+ * runs the paper's pilot -> adaptive-length -> final pipeline for this ROI
+ * (Algorithm 1) with scope CLIP.
+ * h_mass (nullable, host): FP64 total mass sum_n rho_n s_x s_y s_z; giving it
+ * synchronises the stream.
+ * Errors: INVALID_ARG, OOM, CUDA, DEGENERATE (MBE with N_B < 2 or P80 == P20),
+ * EMPTY_ROI (scope CLIP and no point in B; d_out is zero-filled).
+ * Device-side degenerate conditions are reported by the next call that
+ * synchronises (h_mass given, or sf_sync_status).
+ */
+sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], int32_t kernel,
+                      const sf_params *params, float *d_out, double *h_mass, void *stream);
+
+/*
+ * sf_kde_points -- density at every point inside the ROI box (closed).
+ *
+ * Output in ascending original index: d_ids[i] (device uint32) is the
+ * original index of the i-th ROI point and d_density[i] (device float) its
+ * density. capacity = length of both buffers; *h_count (host, required)
+ * receives the number of ROI points (the stream is synchronised). If the
+ * count exceeds capacity, CAPACITY is returned and nothing is written.
+ * DIRECT sums the kernels at each point (the point's own kernel included);
+ * INTERP interpolates the grid of the same dims trilinearly. dims is used by
+ * INTERP and by rule MBE (whose smoothing lengths depend on the grid spacing);
+ * it may be NULL otherwise.
+ */
+sf_status sf_kde_points(sf_index *idx, const sf_box *roi, const int32_t *dims, int32_t kernel,
+                        const sf_params *params, float *d_density, uint32_t *d_ids,
+                        int64_t capacity, int64_t *h_count, void *stream);
+
+/*
+ * sf_select -- density-threshold selection of points (Sec. 4.1).
+ *
+ * Inputs: n densities d_density (device float >= 0) of points with original
+ * indices d_ids (device uint32, ascending, each < n_total).
+ * Threshold t: if `threshold` is not NaN, t = (float)threshold; otherwise t is
+ * the nearest-rank `percentile` (0..100) of the n densities: the value at
+ * 1-based rank ceil(percentile/100 * n) (at least 1) in ascending order.
+ * Selected: every i with density > t (strict).
+ * Outputs: d_mask (device uint8 [n_total], nullable): 1 for selected original
+ * indices, 0 elsewhere; d_sel_ids (device uint32 [n], nullable): the selected
+ * original indices, ascending; *h_nsel (host, nullable) the count and
+ * *h_threshold (host, nullable) the t used -- either synchronises the stream.
+ * n = 0 selects nothing. Errors: INVALID_ARG, OOM, CUDA.
+ */
+sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids, int64_t n,
+                    int64_t n_total, double threshold, double percentile, uint8_t *d_mask,
+                    uint32_t *d_sel_ids, int64_t *h_nsel, double *h_threshold, void *stream);
+
+/* Synchronise `stream` and return (then clear) any status a kernel recorded
+ * on the device for this index (TIMEOUT, DEGENERATE, EMPTY_ROI). */
+sf_status sf_sync_status(sf_index *idx, void *stream);
+
+/* Release the index and all of its device memory. Safe on NULL. */
+void sf_free_index(sf_index *idx);
+
+/* Message describing the last error of the calling thread ("" if none). */
+const char *sf_last_error(void);
+
+/* Number of kernels the library has launched in this process so far. */
+uint64_t sf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCALEFREE_H */

@@ -1,0 +1,216 @@
+"""Thin ctypes binding of libscalefree.so (include/scalefree.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. Functions keep the C names; tensors are passed as device pointers
+(``tensor.data_ptr()``), streams as ``torch.cuda.Stream.cuda_stream`` (or 0).
+There is no CPU fallback: importing this module on a machine without the built
+library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libscalefree.so")
+
+SF_OK = 0
+SF_ERR_INVALID_ARG = 1
+SF_ERR_OOM = 2
+SF_ERR_CUDA = 3
+SF_ERR_TIMEOUT = 4
+SF_ERR_DEGENERATE = 5
+SF_ERR_EMPTY_ROI = 6
+SF_ERR_BUSY = 7
+SF_ERR_CAPACITY = 8
+
+SF_K_EPAN = 0
+SF_K_GAUSS3 = 1
+SF_BW_KNN = 0
+SF_BW_MBE = 1
+SF_BW_FIXED = 2
+SF_SCOPE_CLIP = 0
+SF_SCOPE_GLOBAL = 1
+SF_PREC_FP32 = 0
+SF_POINTS_DIRECT = 0
+SF_POINTS_INTERP = 1
+
+STATUS_NAMES = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_OOM", 3: "SF_ERR_CUDA",
+                4: "SF_ERR_TIMEOUT", 5: "SF_ERR_DEGENERATE", 6: "SF_ERR_EMPTY_ROI",
+                7: "SF_ERR_BUSY", 8: "SF_ERR_CAPACITY"}
+
+
+class sf_box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class sf_params(ctypes.Structure):
+    _fields_ = [("rule", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("fixed_h", ctypes.c_double * 3), ("cap_factor", ctypes.c_double),
+                ("p_lo", ctypes.c_double), ("p_hi", ctypes.c_double),
+                ("log_base", ctypes.c_double), ("scope", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("points_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class SFError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+_PROTOS = {
+    "sf_params_default": (None, [ctypes.POINTER(sf_params)]),
+    "sf_build_index": (ctypes.c_int, [_vp, _i64, _vp, ctypes.POINTER(_vp)]),
+    "sf_index_size": (_i64, [_vp]),
+    "sf_bandwidths": (ctypes.c_int, [_vp, ctypes.POINTER(sf_params), _vp]),
+    "sf_get_bandwidths": (ctypes.c_int, [_vp, _vp, _vp]),
+    "sf_knn_neighbours": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "sf_kde_grid": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
+                                   ctypes.POINTER(sf_params), _vp, ctypes.POINTER(_dbl), _vp]),
+    "sf_kde_points": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
+                                     ctypes.POINTER(sf_params), _vp, _vp, _i64,
+                                     ctypes.POINTER(_i64), _vp]),
+    "sf_select": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, _vp,
+                                 ctypes.POINTER(_i64), ctypes.POINTER(_dbl), _vp]),
+    "sf_sync_status": (ctypes.c_int, [_vp, _vp]),
+    "sf_free_index": (None, [_vp]),
+    "sf_last_error": (ctypes.c_char_p, []),
+    "sf_launch_count": (ctypes.c_uint64, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load libscalefree.so (built by paper_2601_20758_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libscalefree.so not built ({LIB_PATH}); run "
+                               "python -c 'import __graft_entry__ as g; g.build()'")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(fn, st):
+    if st != SF_OK:
+        raise SFError(fn, st, load().sf_last_error().decode())
+    return st
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def make_box(lo, hi) -> sf_box:
+    b = sf_box()
+    for k in range(3):
+        b.lo[k] = float(lo[k])
+        b.hi[k] = float(hi[k])
+    return b
+
+
+def make_params(rule=SF_BW_KNN, k=32, fixed_h=(0.0, 0.0, 0.0), cap_factor=5.0, p_lo=20.0,
+                p_hi=80.0, log_base=0.0, scope=SF_SCOPE_GLOBAL, points_mode=SF_POINTS_DIRECT):
+    p = sf_params()
+    load().sf_params_default(ctypes.byref(p))
+    p.rule, p.k = rule, k
+    for i in range(3):
+        p.fixed_h[i] = float(fixed_h[i])
+    p.cap_factor, p.p_lo, p.p_hi, p.log_base = cap_factor, p_lo, p_hi, log_base
+    p.scope, p.points_mode = scope, points_mode
+    return p
+
+
+# ---------------------------------------------------------------------------
+# Entry points (C names)
+# ---------------------------------------------------------------------------
+def sf_build_index(d_xyz, stream=None):
+    """d_xyz: CUDA float32 tensor [N, 3], contiguous. Returns the index handle."""
+    assert d_xyz.is_cuda and d_xyz.dtype.itemsize == 4 and d_xyz.is_contiguous()
+    h = _vp()
+    _check("sf_build_index", load().sf_build_index(d_xyz.data_ptr(), d_xyz.shape[0],
+                                                   _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def sf_index_size(idx) -> int:
+    return int(load().sf_index_size(idx))
+
+
+def sf_bandwidths(idx, params, stream=None):
+    _check("sf_bandwidths", load().sf_bandwidths(idx, ctypes.byref(params), _stream(stream)))
+
+
+def sf_get_bandwidths(idx, d_h, stream=None):
+    _check("sf_get_bandwidths", load().sf_get_bandwidths(idx, d_h.data_ptr(), _stream(stream)))
+
+
+def sf_knn_neighbours(idx, k, d_nbr, d_h=None, stream=None):
+    _check("sf_knn_neighbours", load().sf_knn_neighbours(
+        idx, int(k), d_nbr.data_ptr(), None if d_h is None else d_h.data_ptr(), _stream(stream)))
+
+
+def sf_kde_grid(idx, roi: sf_box, dims, kernel, params, d_out, want_mass=False, stream=None):
+    """Density on the ROI grid into d_out (float32, dims[2]*dims[1]*dims[0]); returns the
+    FP64 mass when want_mass."""
+    d = (_i32 * 3)(*[int(v) for v in dims])
+    m = _dbl(0.0)
+    _check("sf_kde_grid", load().sf_kde_grid(idx, ctypes.byref(roi), d, int(kernel),
+                                             ctypes.byref(params), d_out.data_ptr(),
+                                             ctypes.byref(m) if want_mass else None,
+                                             _stream(stream)))
+    return m.value if want_mass else None
+
+
+def sf_kde_points(idx, roi: sf_box, dims, kernel, params, d_density, d_ids, stream=None) -> int:
+    """Densities of the ROI points (ascending original index); returns the count."""
+    d = None if dims is None else (_i32 * 3)(*[int(v) for v in dims])
+    cnt = _i64(0)
+    _check("sf_kde_points", load().sf_kde_points(idx, ctypes.byref(roi), d, int(kernel),
+                                                 ctypes.byref(params), d_density.data_ptr(),
+                                                 d_ids.data_ptr(), d_density.numel(),
+                                                 ctypes.byref(cnt), _stream(stream)))
+    return int(cnt.value)
+
+
+def sf_select(idx, d_density, d_ids, n, n_total, threshold=math.nan, percentile=90.0,
+              d_mask=None, d_sel_ids=None, stream=None):
+    """Returns (count, threshold used)."""
+    ns = _i64(0)
+    t = _dbl(0.0)
+    _check("sf_select", load().sf_select(
+        idx, None if d_density is None else d_density.data_ptr(),
+        None if d_ids is None else d_ids.data_ptr(), int(n), int(n_total), float(threshold),
+        float(percentile), None if d_mask is None else d_mask.data_ptr(),
+        None if d_sel_ids is None else d_sel_ids.data_ptr(), ctypes.byref(ns), ctypes.byref(t),
+        _stream(stream)))
+    return int(ns.value), float(t.value)
+
+
+def sf_sync_status(idx, stream=None) -> int:
+    return int(load().sf_sync_status(idx, _stream(stream)))
+
+
+def sf_free_index(idx):
+    load().sf_free_index(idx)
+
+
+def sf_last_error() -> str:
+    return load().sf_last_error().decode()
+
+
+def sf_launch_count() -> int:
+    return int(load().sf_launch_count())
