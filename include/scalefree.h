@@ -208,6 +208,29 @@ sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids
                     int64_t n_total, double threshold, double percentile, uint8_t *d_mask,
                     uint32_t *d_sel_ids, int64_t *h_nsel, double *h_threshold, void *stream);
 
+/*
+ * sf_count_support_pairs -- the algorithmic work of one ROI recompute: the
+ * number of (grid node, particle) pairs (h_grid_pairs, needs dims) and of
+ * (ROI point, particle) pairs (h_point_pairs, DIRECT) whose kernel value is
+ * non-zero (q < 1 for EPAN, q < 9 for GAUSS3), counted by the same kernels as
+ * sf_kde_grid / sf_kde_points in a counting variant (slower; not for timing).
+ * Either output may be NULL. Synchronises the stream.
+ */
+sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t dims[3],
+                                 int32_t kernel, const sf_params *params, int64_t *h_grid_pairs,
+                                 int64_t *h_point_pairs, void *stream);
+
+/*
+ * Kernel timing: when enabled, the main kernels (k_grid, k_points, k_knn,
+ * k_radix_sort, and the counting variants) are bracketed by CUDA events on the
+ * stream they are launched on. sf_kernel_timing sums the elapsed times and
+ * counts the launches recorded under `name` since the last reset (it waits for
+ * the recorded events). Off by default; enabling adds event records only.
+ */
+void sf_kernel_timing_enable(int enable);
+void sf_kernel_timing_reset(void);
+sf_status sf_kernel_timing(const char *name, double *h_ms_total, int64_t *h_launches);
+
 /* Synchronise `stream` and return (then clear) any status a kernel recorded
  * on the device for this index (TIMEOUT, DEGENERATE, EMPTY_ROI). */
 sf_status sf_sync_status(sf_index *idx, void *stream);

@@ -311,6 +311,43 @@ sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids
                          h_nsel, h_threshold, (cudaStream_t)stream);
 }
 
+sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t dims[3],
+                                 int32_t kernel, const sf_params *params, int64_t *h_grid_pairs,
+                                 int64_t *h_point_pairs, void *stream) {
+    clear_error();
+    if (!idx || (!h_grid_pairs && !h_point_pairs))
+        return fail(SF_ERR_INVALID_ARG, "sf_count_support_pairs: NULL argument");
+    SF_TRY(check_roi(roi, "sf_count_support_pairs"));
+    SF_TRY(check_params(idx, params, kernel, "sf_count_support_pairs"));
+    GridSpec g;
+    const bool need_grid = h_grid_pairs || params->rule == SF_BW_MBE;
+    if (need_grid) SF_TRY(make_grid(*roi, dims, g, "sf_count_support_pairs"));
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    unsigned long long *cnt = sc.get<unsigned long long>(2);
+    SF_TRY_SCRATCH(sc);
+    SF_TRY_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
+    Prepared pr;
+    SF_TRY(prepare(idx, *roi, need_grid ? &g : nullptr, kernel, *params, sc, pr, s));
+    if (h_grid_pairs) {
+        float *grid = sc.get<float>((int64_t)g.nx * g.ny * g.nz);
+        SF_TRY_SCRATCH(sc);
+        SF_TRY(density_grid(idx, *roi, g, pr.call, grid, nullptr, s, cnt));
+    }
+    if (h_point_pairs) {
+        float *rho = sc.get<float>(idx->n);
+        uint8_t *inroi = sc.get<uint8_t>(idx->n);
+        SF_TRY_SCRATCH(sc);
+        SF_TRY(density_points(idx, *roi, pr.call, rho, inroi, s, cnt + 1));
+    }
+    unsigned long long h[2] = {0, 0};
+    SF_TRY_CUDA(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, s));
+    SF_TRY_CUDA(cudaStreamSynchronize(s));
+    if (h_grid_pairs) *h_grid_pairs = (int64_t)h[0];
+    if (h_point_pairs) *h_point_pairs = (int64_t)h[1];
+    return sf_sync_status(idx, stream);
+}
+
 sf_status sf_sync_status(sf_index *idx, void *stream) {
     if (!idx) return fail(SF_ERR_INVALID_ARG, "sf_sync_status: NULL index");
     cudaStream_t s = (cudaStream_t)stream;

@@ -193,6 +193,7 @@ struct GridArgs {
     int tiles_x, tiles_y, tiles_z;
     float *out;
     double *mass_part;   // per tile, sum of rho (before the cell volume)
+    unsigned long long *pairs;  // counting variant: in-support (voxel, particle) pairs
 };
 
 struct GridSmem {
@@ -212,7 +213,7 @@ struct GridSmem {
     double red[kGridThreads / 32];
 };
 
-template <int KER, int BW, bool CLIP>
+template <int KER, int BW, bool CLIP, bool CNT>
 __global__ void __launch_bounds__(kGridThreads, 2) k_grid(GridArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GridSmem &S = *reinterpret_cast<GridSmem *>(smem_raw);
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_grid(GridArgs a) {
     auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, S.uni, node, tlo, thi); };
 
     const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
+    unsigned long long npairs = 0;
     float acc[kTileZ], sum[kTileZ], cmp[kTileZ];
 #pragma unroll
     for (int k = 0; k < kTileZ; ++k) acc[k] = sum[k] = cmp[k] = 0.f;
@@ -412,7 +414,10 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_grid(GridArgs a) {
                     for (int k = 0; k < kTileZ; ++k) {
                         if (k >= z0 && k <= z1) {
                             const float2 ez = S.tz[s][k];
-                            if (qij < ez.y) acc[k] = fmaf(base, ez.x, acc[k]);
+                            if (qij < ez.y) {
+                                acc[k] = fmaf(base, ez.x, acc[k]);
+                                if (CNT) ++npairs;
+                            }
                         }
                     }
                 } else {
@@ -422,6 +427,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_grid(GridArgs a) {
                         if (k >= z0 && k <= z1) {
                             const float t = S.tz[s][k].x - b;
                             acc[k] += fmaxf(t, 0.f);
+                            if (CNT) npairs += (t > 0.f);
                         }
                     }
                 }
@@ -440,6 +446,12 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_grid(GridArgs a) {
         if (!more) break;
     }
 
+    if (CNT) {
+        if (cx >= nvx || cy >= nvy) npairs = 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        if (lane == 0 && npairs) atomicAdd(a.pairs, npairs);
+    }
     // ---- write the tile and its mass
     double msum = 0.0;
     const double inv_neff = S.inv_neff;
@@ -483,17 +495,24 @@ __global__ void k_mass_final(const double *__restrict__ part, int64_t n, double 
     }
 }
 
-template <int KER, int BW, bool CLIP>
-static cudaError_t launch_grid(const GridArgs &a, unsigned tiles, cudaStream_t s) {
+template <int KER, int BW, bool CLIP, bool CNT>
+static cudaError_t launch_grid_t(const GridArgs &a, unsigned tiles, cudaStream_t s) {
     const size_t smem = sizeof(GridSmem);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_grid<KER, BW, CLIP>,
+        cudaError_t e = cudaFuncSetAttribute(k_grid<KER, BW, CLIP, CNT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    return launch(k_grid<KER, BW, CLIP>, dim3(tiles), dim3(kGridThreads), smem, s, a);
+    KTimer t(CNT ? "k_grid_count" : "k_grid", s);
+    return launch(k_grid<KER, BW, CLIP, CNT>, dim3(tiles), dim3(kGridThreads), smem, s, a);
+}
+
+template <int KER, int BW, bool CLIP>
+static cudaError_t launch_grid(const GridArgs &a, unsigned tiles, cudaStream_t s) {
+    return a.pairs ? launch_grid_t<KER, BW, CLIP, true>(a, tiles, s)
+                   : launch_grid_t<KER, BW, CLIP, false>(a, tiles, s);
 }
 
 template <int KER>
@@ -528,7 +547,8 @@ static EngineArgs engine_args(sf_index *idx, const sf_box &roi, const DensityCal
 }
 
 sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
-                       const DensityCall &call, float *d_out, double *d_mass, cudaStream_t s) {
+                       const DensityCall &call, float *d_out, double *d_mass, cudaStream_t s,
+                       unsigned long long *d_pairs) {
     // node coordinates r_k(i) = lo_k + i s_k in double, split into float (hi, lo)
     std::vector<float2> ax((size_t)g.nx + g.ny + g.nz);
     const int nd[3] = {g.nx, g.ny, g.nz};
@@ -558,6 +578,7 @@ sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
     a.axis = d_axis;
     a.out = d_out;
     a.mass_part = mass_part;
+    a.pairs = d_pairs;
     cudaError_t e = (call.kernel == SF_K_EPAN)
                         ? dispatch_grid<SF_K_EPAN>(call.bw, call.clip != 0, a, (unsigned)tiles, s)
                         : dispatch_grid<SF_K_GAUSS3>(call.bw, call.clip != 0, a, (unsigned)tiles, s);
@@ -579,6 +600,7 @@ struct PointsArgs {
     EngineArgs e;
     float *rho_sorted;
     uint8_t *inroi;
+    unsigned long long *pairs;  // counting variant
 };
 
 struct PtWarpSmem {
@@ -588,7 +610,7 @@ struct PtWarpSmem {
     float4 su[kLeaf];
 };
 
-template <int KER, int BW, bool CLIP>
+template <int KER, int BW, bool CLIP, bool CNT>
 __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
     __shared__ PtWarpSmem W[kPtWarps];
     __shared__ float s_uni[3];
@@ -627,6 +649,7 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
     auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, s_uni, node, tlo, thi); };
 
     float sum = 0.f, cmp = 0.f;
+    unsigned long long npairs = 0;
     int spv;
     int nl = warp_walk_start(a.e.tv, test, S.stack, spv, S.leaves);
     while (true) {
@@ -678,6 +701,7 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
                 if (qq < KDef<KER>::qmax) {
                     if (KER == SF_K_GAUSS3) acc = fmaf(P.w, ex2_approx(-qq), acc);
                     else acc = fmaf(P.w, 1.0f - qq, acc);
+                    if (CNT) ++npairs;
                 }
             }
             __syncwarp();
@@ -689,12 +713,24 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
         nl = 0;
     }
     if (active) a.rho_sorted[qi] = (float)(((double)sum + (double)cmp) * s_inv);
+    if (CNT) {
+        if (!active) npairs = 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        if (lane == 0 && npairs) atomicAdd(a.pairs, npairs);
+    }
 }
 
 template <int KER, int BW, bool CLIP>
 static cudaError_t launch_points(const PointsArgs &a, int64_t nleaf, cudaStream_t s) {
-    return launch(k_points<KER, BW, CLIP>, dim3(blocks_for(nleaf, kPtWarps)), dim3(kPtWarps * 32),
-                  0, s, a);
+    if (a.pairs) {
+        KTimer t("k_points_count", s);
+        return launch(k_points<KER, BW, CLIP, true>, dim3(blocks_for(nleaf, kPtWarps)),
+                      dim3(kPtWarps * 32), 0, s, a);
+    }
+    KTimer t("k_points", s);
+    return launch(k_points<KER, BW, CLIP, false>, dim3(blocks_for(nleaf, kPtWarps)),
+                  dim3(kPtWarps * 32), 0, s, a);
 }
 
 template <int KER>
@@ -711,11 +747,13 @@ static cudaError_t dispatch_points(int bw, bool clip, const PointsArgs &a, int64
 }
 
 sf_status density_points(sf_index *idx, const sf_box &roi, const DensityCall &call,
-                         float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s) {
+                         float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s,
+                         unsigned long long *d_pairs) {
     PointsArgs a;
     a.e = engine_args(idx, roi, call);
     a.rho_sorted = d_rho_sorted;
     a.inroi = d_inroi;
+    a.pairs = d_pairs;
     cudaError_t e = (call.kernel == SF_K_EPAN)
                         ? dispatch_points<SF_K_EPAN>(call.bw, call.clip != 0, a, idx->cnt[0], s)
                         : dispatch_points<SF_K_GAUSS3>(call.bw, call.clip != 0, a, idx->cnt[0], s);

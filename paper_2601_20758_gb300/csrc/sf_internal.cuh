@@ -47,6 +47,16 @@ inline cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
     return cudaGetLastError();
 }
 
+// Optional CUDA-event timing of named kernels on their launching stream
+// (enabled with sf_kernel_timing_enable; off by default, then a no-op).
+struct KTimer {
+    const char *name;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KTimer(const char *n, cudaStream_t st);
+    ~KTimer();
+};
+
 inline unsigned blocks_for(int64_t n, int per_block) {
     return (unsigned)((n + per_block - 1) / per_block);
 }
@@ -209,12 +219,14 @@ struct DensityCall {
 };
 
 sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
-                       const DensityCall &call, float *d_out, double *d_mass, cudaStream_t s);
+                       const DensityCall &call, float *d_out, double *d_mass, cudaStream_t s,
+                       unsigned long long *d_pairs = nullptr);
 
 // Density at the sorted points inside roi (DIRECT). d_rho_sorted[i] for sorted
 // i in roi, d_inroi[i] = 1/0. d_count receives the number of roi points.
 sf_status density_points(sf_index *idx, const sf_box &roi, const DensityCall &call,
-                         float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s);
+                         float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s,
+                         unsigned long long *d_pairs = nullptr);
 
 // Node max smoothing length per axis for BW_ISO (from pos.w) or BW_ANISO (from ell,
 // only points inside roi when clip) into d_nell.

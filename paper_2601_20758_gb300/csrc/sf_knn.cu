@@ -26,13 +26,14 @@ namespace sf {
 constexpr int kKnnWarps = 4;
 constexpr int kNB = 32;        // histogram bins per lane
 constexpr int kBand = 16;      // band buffer per lane
-constexpr int kKBatch = 64;    // leaves per traversal batch
+constexpr int kCand = 256;     // cached candidate leaves per warp
 constexpr int kKStack = 32 * kMaxLevels;
 constexpr float kDelta = 2.0e-6f;
 
 struct KnnWarpSmem {
     int stack[kKStack];
-    int leaves[kKBatch];
+    int cand[kCand];
+    float4 blo[32], bhi[32];   // child boxes under test
     float4 pts[kLeaf];
     uint32_t ids[kLeaf];
     uint32_t hist[kNB][32];
@@ -64,93 +65,143 @@ __device__ __forceinline__ bool key_less(double da, uint32_t ia, double db, uint
     return da < db || (da == db && ia < ib);
 }
 
-// Is any point of node i within sqrt(r2) of the box [qlo, qhi]? (conservative)
-__device__ __forceinline__ bool node_near(const TreeView &tv, int64_t i, const float qlo[3],
-                                          const float qhi[3], float r2) {
-    const float4 lo = __ldg(&tv.nlo[i]);
-    const float4 hi = __ldg(&tv.nhi[i]);
-    const float nl[3] = {lo.x, lo.y, lo.z}, nh[3] = {hi.x, hi.y, hi.z};
-    float d2 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        float gap = fmaxf(fmaxf(nl[k] - qhi[k], qlo[k] - nh[k]), 0.f);
-        gap = fmaxf(gap - 1.0e-6f * (fabsf(qlo[k]) + fabsf(qhi[k])), 0.f);
-        d2 = fmaf(gap, gap, d2);
-    }
-    return d2 <= r2 * (1.0f + 1.0e-5f);
-}
+// Per-warp state of the candidate search: every lane holds one query point and
+// its squared search radius r2 (negative: the lane takes no part).
+struct KnnWarp {
+    const TreeView &tv;
+    const uint32_t *perm;
+    KnnWarpSmem &S;
+    float4 q;
+    float r2;                   // squared radius of this lane's ball
+    float env_lo[3], env_hi[3]; // warp envelope of all balls
+    int ncand;
+    bool overflow;
 
-// Same resumable walk as the density engine (duplicated here to keep the
-// translation units independent).
-template <typename Test>
-__device__ int knn_walk(const TreeView &tv, const Test &test, int *stack, int &sp, int *out,
-                        int cap) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int nout = 0;
-    while (sp > 0 && nout <= cap - 32) {
-        const int e = stack[sp - 1];
-        __syncwarp();
-        sp -= 1;
-        const int cl = (e >> 27) - 1;
-        const int64_t c = (int64_t)(e & ((1 << 27) - 1)) * kFanout + lane;
-        const bool ok = (c < tv.cnt[cl]) && test(tv.off[cl] + c);
-        const unsigned m = __ballot_sync(0xffffffffu, ok);
-        const int r = __popc(m & lt), kk = __popc(m);
-        if (cl == 0) {
-            if (ok) out[nout + r] = (int)c;
-            nout += kk;
-        } else {
-            if (ok) stack[sp + (kk - 1 - r)] = (cl << 27) | (int)c;
-            sp += kk;
+    __device__ KnnWarp(const TreeView &t, const uint32_t *p, KnnWarpSmem &s) : tv(t), perm(p), S(s) {}
+
+    // Mask of the children (lane c holds child c at level cl) that lie within
+    // the ball of at least one lane. Conservative: relative slack 1e-5.
+    __device__ unsigned accept(int cl, int64_t c, bool valid) {
+        const int lane = threadIdx.x & 31;
+        bool pre = false;
+        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+        if (valid) {
+            lo = __ldg(&tv.nlo[tv.off[cl] + c]);
+            hi = __ldg(&tv.nhi[tv.off[cl] + c]);
+            pre = lo.x <= env_hi[0] && hi.x >= env_lo[0] && lo.y <= env_hi[1] && hi.y >= env_lo[1] &&
+                  lo.z <= env_hi[2] && hi.z >= env_lo[2];
+        }
+        unsigned m = __ballot_sync(0xffffffffu, pre);
+        if (pre) {
+            S.blo[lane] = lo;
+            S.bhi[lane] = hi;
         }
         __syncwarp();
-    }
-    return nout;
-}
-
-// Visit every point of every leaf the walk accepts, in traversal order:
-// fn(point float4, original id, sorted index) is called by every lane for each
-// of the (up to) 32 points of a leaf (the same point on all lanes).
-template <typename Test, typename Fn>
-__device__ void for_each_candidate(const KnnArgs &a, KnnWarpSmem &S, const Test &test, Fn fn) {
-    const int lane = threadIdx.x & 31;
-    const TreeView &tv = a.tv;
-    const int top = tv.nlevels - 1;
-    int sp = 0;
-    int nl = 0;
-    const bool root_ok = __shfl_sync(0xffffffffu, lane == 0 ? (int)test(tv.off[top]) : 0, 0) != 0;
-    if (!root_ok) return;
-    if (top == 0) {
-        if (lane == 0) S.leaves[0] = 0;
-        __syncwarp();
-        nl = 1;
-    } else {
-        if (lane == 0) S.stack[0] = top << 27;
-        __syncwarp();
-        sp = 1;
-    }
-    while (true) {
-        if (nl == 0) {
-            if (sp == 0) break;
-            nl = knn_walk(tv, test, S.stack, sp, S.leaves, kKBatch);
-            if (nl == 0) break;
+        unsigned acc = 0;
+        const float lim = r2 * (1.0f + 1.0e-5f);
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const float4 bl = S.blo[j], bh = S.bhi[j];
+            const float gx = fmaxf(fmaxf(bl.x - q.x, q.x - bh.x), 0.f);
+            const float gy = fmaxf(fmaxf(bl.y - q.y, q.y - bh.y), 0.f);
+            const float gz = fmaxf(fmaxf(bl.z - q.z, q.z - bh.z), 0.f);
+            const float d2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+            if (__any_sync(0xffffffffu, r2 >= 0.f && d2 <= lim)) acc |= 1u << j;
         }
-        for (int li = 0; li < nl; ++li) {
-            const int64_t base = (int64_t)S.leaves[li] * kLeaf;
-            const int64_t j = base + lane;
-            if (j < tv.n) {
-                S.pts[lane] = __ldg(&tv.pos[j]);
-                S.ids[lane] = __ldg(&a.perm[j]);
+        __syncwarp();
+        return acc;
+    }
+
+    // Resumable walk: appends accepted leaves to S.cand until fewer than 32
+    // slots remain or the stack is empty.
+    __device__ int walk(int &sp) {
+        const int lane = threadIdx.x & 31;
+        const unsigned lt = (1u << lane) - 1u;
+        int nout = 0;
+        while (sp > 0 && nout <= kCand - 32) {
+            const int e = S.stack[sp - 1];
+            __syncwarp();
+            sp -= 1;
+            const int cl = (e >> 27) - 1;
+            const int64_t c = (int64_t)(e & ((1 << 27) - 1)) * kFanout + lane;
+            const unsigned m = accept(cl, c, c < tv.cnt[cl]);
+            const bool ok = (m >> lane) & 1u;
+            const int r = __popc(m & lt), kk = __popc(m);
+            if (cl == 0) {
+                if (ok) S.cand[nout + r] = (int)c;
+                nout += kk;
+            } else {
+                if (ok) S.stack[sp + (kk - 1 - r)] = (cl << 27) | (int)c;
+                sp += kk;
             }
             __syncwarp();
-            const int cnt = (int)(tv.n - base < kLeaf ? tv.n - base : kLeaf);
-            for (int t = 0; t < cnt; ++t) fn(S.pts[t], S.ids[t], base + t);
-            __syncwarp();
         }
-        nl = 0;
+        return nout;
     }
-}
+
+    __device__ int start(int &sp) {
+        const int top = tv.nlevels - 1;
+        if (top == 0) {
+            sp = 0;
+            if ((threadIdx.x & 31) == 0) S.cand[0] = 0;
+            __syncwarp();
+            return 1;
+        }
+        if ((threadIdx.x & 31) == 0) S.stack[0] = top << 27;
+        __syncwarp();
+        sp = 1;
+        return 0;
+    }
+
+    // Build the candidate leaf list once; if it does not fit, later passes walk again.
+    __device__ void collect() {
+        int sp;
+        ncand = start(sp);
+        if (sp > 0) ncand = walk(sp);
+        overflow = sp > 0;
+    }
+
+    __device__ void load_leaf(int64_t leaf) {
+        const int lane = threadIdx.x & 31;
+        const int64_t j = leaf * kLeaf + lane;
+        if (j < tv.n) {
+            S.pts[lane] = __ldg(&tv.pos[j]);
+            S.ids[lane] = __ldg(&perm[j]);
+        }
+        __syncwarp();
+    }
+
+    // fn(point, original id, sorted index) for every point of every candidate leaf.
+    template <typename Fn>
+    __device__ void each(Fn fn) {
+        auto leaves = [&](int n) {
+            for (int li = 0; li < n; ++li) {
+                const int64_t L = S.cand[li];
+                load_leaf(L);
+                const int64_t base = L * kLeaf;
+                const int cnt = (int)(tv.n - base < kLeaf ? tv.n - base : kLeaf);
+                for (int t = 0; t < cnt; ++t) fn(S.pts[t], S.ids[t], base + t);
+                __syncwarp();
+            }
+        };
+        if (!overflow) {
+            leaves(ncand);
+            return;
+        }
+        int sp;
+        int n = start(sp);
+        while (true) {
+            if (n == 0) {
+                if (sp == 0) break;
+                n = walk(sp);
+                if (n == 0) break;
+            }
+            leaves(n);
+            n = 0;
+        }
+    }
+};
 
 __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -162,15 +213,29 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
     const int k = a.k;
     const int64_t qi = leaf * kLeaf + lane;
     const bool valid = qi < tv.n;
-    const float4 q = valid ? __ldg(&tv.pos[qi]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    KnnWarp W(tv, a.perm, S);
+    W.q = valid ? __ldg(&tv.pos[qi]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 q = W.q;
     const uint32_t qid = valid ? __ldg(&a.perm[qi]) : 0u;
 
     auto clear_hist = [&]() {
         for (int b = 0; b < kNB; ++b) S.hist[b][lane] = 0;
         __syncwarp();
     };
+    // bin search: smallest bin b with below + cum(hist[0..b]) >= k
+    auto bracket = [&](int below, int &b_out, int &before) {
+        int cum = below, b = 0;
+        for (; b < kNB - 1; ++b) {
+            const int c = S.hist[b][lane];
+            if (cum + c >= k) break;
+            cum += c;
+        }
+        b_out = b;
+        before = cum;
+    };
 
-    // ---- 1. radius bound from the neighbouring leaves in sorted order
+    // ---- 1. radius bound: k-th smallest d2 among the leaves next in sorted order,
+    //         bracketed by three rounds of 32-bin histograms
     const int64_t nleaf = tv.cnt[0];
     const int64_t wl = (int64_t)((k + 1 + 31) / 32) + 2;
     int64_t w0 = leaf - wl / 2, w1;
@@ -190,93 +255,95 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
             __syncwarp();
         }
     };
-    float wmax = 0.f;
+    float wlo = 0.f, whi = 0.f;
     window_visit([&](float4 p, int64_t j) {
-        if (j != qi) wmax = fmaxf(wmax, d2_f32(q, p));
+        if (j != qi) whi = fmaxf(whi, d2_f32(q, p));
     });
-    clear_hist();
-    const float winv = wmax > 0.f ? (float)kNB / wmax : 0.f;
-    window_visit([&](float4 p, int64_t j) {
-        if (valid && j != qi) {
-            const int b = min(kNB - 1, (int)(d2_f32(q, p) * winv));
-            S.hist[b][lane] += 1;
-        }
-    });
-    __syncwarp();
-    float T = 0.f;  // squared radius holding at least k points
-    {
-        int cum = 0, b = 0;
+    for (int round = 0; round < 3; ++round) {
+        clear_hist();
+        const float width = whi - wlo;
+        const float inv = width > 0.f ? (float)kNB / width : 0.f;
+        int below = 0;
+        window_visit([&](float4 p, int64_t j) {
+            if (j != qi) {
+                const float d = d2_f32(q, p);
+                if (d < wlo) ++below;
+                else if (d <= whi) S.hist[min(kNB - 1, (int)((d - wlo) * inv))][lane] += 1;
+            }
+        });
+        __syncwarp();
+        int cum = below, b = 0;
         for (; b < kNB; ++b) {
-            cum += S.hist[b][lane];
-            if (cum >= k) break;
+            const int c = S.hist[b][lane];
+            if (cum + c >= k) break;
+            cum += c;
         }
-        const float edge = (b >= kNB - 1) ? wmax : (float)(b + 1) * (wmax / (float)kNB);
-        T = edge * (1.0f + 4.0e-6f) + 1.0e-37f;
+        // keep the current bracket if rounding left the k-th outside it
+        if (b < kNB && width > 0.f) {
+            const float nlo = (wlo + (float)b * (width / (float)kNB)) * (1.0f - 1.0e-6f);
+            const float nhi = (b == kNB - 1 ? whi : wlo + (float)(b + 1) * (width / (float)kNB)) *
+                              (1.0f + 1.0e-6f);
+            wlo = fmaxf(nlo, 0.f);
+            whi = fminf(nhi, whi);
+        }
     }
-    if (!valid) T = 0.f;
+    const float T = valid ? whi * (1.0f + 4.0e-6f) + 1.0e-37f : -1.f;
 
-    // query box and traversal radius (warp-wide)
-    float qlo[3] = {valid ? q.x : INFINITY, valid ? q.y : INFINITY, valid ? q.z : INFINITY};
-    float qhi[3] = {valid ? q.x : -INFINITY, valid ? q.y : -INFINITY, valid ? q.z : -INFINITY};
-    float Tmax = T;
+    // ---- 2. candidate leaves: within sqrt(T) of at least one lane's point
+    W.r2 = T;
+    {
+        const float r = valid ? sqrtf(T) * (1.0f + 1.0e-5f) : 0.f;
+        float lo3[3] = {valid ? q.x - r : INFINITY, valid ? q.y - r : INFINITY, valid ? q.z - r : INFINITY};
+        float hi3[3] = {valid ? q.x + r : -INFINITY, valid ? q.y + r : -INFINITY, valid ? q.z + r : -INFINITY};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        Tmax = fmaxf(Tmax, __shfl_xor_sync(0xffffffffu, Tmax, o));
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo3[d] = fminf(lo3[d], __shfl_xor_sync(0xffffffffu, lo3[d], o));
+                hi3[d] = fmaxf(hi3[d], __shfl_xor_sync(0xffffffffu, hi3[d], o));
+            }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            qlo[d] = fminf(qlo[d], __shfl_xor_sync(0xffffffffu, qlo[d], o));
-            qhi[d] = fmaxf(qhi[d], __shfl_xor_sync(0xffffffffu, qhi[d], o));
+            W.env_lo[d] = lo3[d];
+            W.env_hi[d] = hi3[d];
         }
     }
-    auto test = [&](int64_t node) { return node_near(tv, node, qlo, qhi, Tmax); };
+    W.collect();
 
-    // ---- 2./3. histogram and band passes, refined until the band fits
-    float lo_e = 0.f, hi_e = T;  // current bracket [lo_e, hi_e] in FP32 d2
-    int below_base = 0;          // points with d2 < lo_e (exact side, see margins)
+    // ---- 3. histogram and band passes, refined until the band fits
+    float lo_e = 0.f, hi_e = valid ? T : 0.f;
     bool done = !valid;
     int need = 0;
     double kth = 0.0;
-    bool extract = false;        // fallback: extract band members one by one
+    bool extract = false;
     float band_lo = 0.f, band_hi = 0.f;
     int nb_below = 0;
     for (int round = 0; round < 8; ++round) {
-        const bool any = __any_sync(0xffffffffu, !done && !extract);
-        if (!any) break;
-        // histogram of d2 within [lo_e, hi_e]
+        if (!__any_sync(0xffffffffu, !done && !extract)) break;
         clear_hist();
         const float width = hi_e - lo_e;
         const float inv = width > 0.f ? (float)kNB / width : 0.f;
         const bool act = !done && !extract;
         int below = 0;
-        for_each_candidate(a, S, test, [&](float4 p, uint32_t, int64_t j) {
+        W.each([&](float4 p, uint32_t, int64_t j) {
             if (act && j != qi) {
                 const float d = d2_f32(q, p);
                 if (d < lo_e) ++below;
-                else if (d <= hi_e) {
-                    const int b = min(kNB - 1, (int)((d - lo_e) * inv));
-                    S.hist[b][lane] += 1;
-                }
+                else if (d <= hi_e) S.hist[min(kNB - 1, (int)((d - lo_e) * inv))][lane] += 1;
             }
         });
         __syncwarp();
         float e_lo = lo_e, e_hi = hi_e;
         if (act) {
-            int cum = below, b = 0;
-            for (; b < kNB; ++b) {
-                const int c = S.hist[b][lane];
-                if (cum + c >= k) break;
-                cum += c;
-            }
-            if (b >= kNB) b = kNB - 1;  // cannot happen: T bounds the k-th
+            int b, before;
+            bracket(below, b, before);
             e_lo = lo_e + (float)b * (width / (float)kNB);
             e_hi = (b == kNB - 1) ? hi_e : lo_e + (float)(b + 1) * (width / (float)kNB);
-            below_base = below;
+            band_lo = e_lo * (1.0f - kDelta);
+            band_hi = e_hi * (1.0f + kDelta);
         }
-        // band pass
-        band_lo = e_lo * (1.0f - kDelta);
-        band_hi = e_hi * (1.0f + kDelta);
         int nbelow = 0, nband = 0;
-        for_each_candidate(a, S, test, [&](float4 p, uint32_t id, int64_t j) {
+        W.each([&](float4 p, uint32_t id, int64_t j) {
             if (act && j != qi) {
                 const float d = d2_f32(q, p);
                 if (d < band_lo) ++nbelow;
@@ -294,7 +361,6 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
             need = k - nbelow;
             nb_below = nbelow;
             if (nband <= kBand) {
-                // sort the band by (d2, id), take the need-th
                 for (int x = 1; x < nband; ++x) {
                     const double dv = S.bd[x][lane];
                     const uint32_t iv = S.bi[x][lane];
@@ -329,7 +395,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
             const bool act = extract && got < need;
             double best_d = INFINITY;
             uint32_t best_i = 0xffffffffu;
-            for_each_candidate(a, S, test, [&](float4 p, uint32_t id, int64_t j) {
+            W.each([&](float4 p, uint32_t id, int64_t j) {
                 if (act && j != qi) {
                     const float d = d2_f32(q, p);
                     if (d >= band_lo && d <= band_hi) {
@@ -360,7 +426,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
     // ---- optional neighbour ids: the below set, then the band's first `need`
     if (a.nbr_orig) {
         int slot = 0;
-        for_each_candidate(a, S, test, [&](float4 p, uint32_t id, int64_t j) {
+        W.each([&](float4 p, uint32_t id, int64_t j) {
             if (valid && j != qi) {
                 const float d = d2_f32(q, p);
                 if (d < band_lo && slot < k) a.nbr_orig[(int64_t)qid * k + slot++] = id;
@@ -405,6 +471,7 @@ sf_status knn_run(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_sorted,
         SF_TRY_CUDA(cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
+    KTimer timer("k_knn", s);
     SF_TRY_CUDA(launch(k_knn, dim3(blocks_for(idx->cnt[0], kKnnWarps)), dim3(kKnnWarps * 32), smem,
                        s, a));
     return SF_OK;

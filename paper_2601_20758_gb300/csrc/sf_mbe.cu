@@ -22,7 +22,7 @@ sf_status set_density_params(sf_index *idx, bool clip, const sf_box &roi, const 
 
 struct InterpGrid {
     int nx, ny, nz;
-    float lo[3], inv_s[3];
+    double lo[3], inv_s[3];
 };
 
 static InterpGrid interp_grid(const GridSpec &g) {
@@ -31,24 +31,27 @@ static InterpGrid interp_grid(const GridSpec &g) {
     ig.ny = g.ny;
     ig.nz = g.nz;
     for (int k = 0; k < 3; ++k) {
-        ig.lo[k] = (float)g.lo[k];
-        ig.inv_s[k] = (float)(1.0 / g.s[k]);
+        ig.lo[k] = g.lo[k];
+        ig.inv_s[k] = 1.0 / g.s[k];
     }
     return ig;
 }
 
+// The position in the grid is formed in FP64 (three subtractions and products
+// per point) so that the weights carry no cancellation from large coordinates.
 __device__ __forceinline__ float trilinear(const float *__restrict__ grid, const InterpGrid &g,
                                            float x, float y, float z) {
-    const float u[3] = {(x - g.lo[0]) * g.inv_s[0], (y - g.lo[1]) * g.inv_s[1], (z - g.lo[2]) * g.inv_s[2]};
+    const double u[3] = {((double)x - g.lo[0]) * g.inv_s[0], ((double)y - g.lo[1]) * g.inv_s[1],
+                         ((double)z - g.lo[2]) * g.inv_s[2]};
     const int n[3] = {g.nx, g.ny, g.nz};
     int i[3];
     float t[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int c = (int)floorf(u[k]);
+        int c = (int)floor(u[k]);
         c = min(max(c, 0), n[k] - 2);
         i[k] = c;
-        t[k] = u[k] - (float)c;
+        t[k] = (float)(u[k] - (double)c);
     }
     const int64_t sx = 1, sy = g.nx, sz = (int64_t)g.nx * g.ny;
     const float *b = grid + i[2] * sz + i[1] * sy + i[0] * sx;

@@ -27,6 +27,33 @@ const char *last_error_cstr() { return t_last_error.c_str(); }
 void clear_error() { t_last_error.clear(); }
 
 // ---------------------------------------------------------------------------
+// Kernel timing registry: event pairs recorded on the launching stream.
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_timing{0};
+static std::mutex g_timing_mu;
+struct TimedPair {
+    std::string name;
+    cudaEvent_t a, b;
+};
+static std::vector<TimedPair> g_timed;
+
+KTimer::KTimer(const char *n, cudaStream_t st) : name(n), s(st) {
+    if (!g_timing.load(std::memory_order_relaxed)) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        a = b = nullptr;
+        return;
+    }
+    cudaEventRecord(a, s);
+}
+
+KTimer::~KTimer() {
+    if (!a) return;
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_timed.push_back({name, a, b});
+}
+
+// ---------------------------------------------------------------------------
 // Block-level helpers
 // ---------------------------------------------------------------------------
 // Exclusive scan of one uint32 per thread across a block of blockDim.x (multiple
@@ -231,6 +258,7 @@ sf_status radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_tmp,
     Scratch sc(s);
     uint32_t *counts = sc.get<uint32_t>(256 * nb);
     SF_TRY_SCRATCH(sc);
+    KTimer timer("k_radix_sort", s);
     int passes = (bits + 7) / 8;
     if (passes & 1) ++passes;  // even number of passes: result lands back in (keys, vals)
     uint64_t *ka = keys, *kb = keys_tmp;
@@ -324,3 +352,35 @@ sf_status radix_select_u32(const uint32_t *d_keys, int64_t n, const int64_t *d_r
 }
 
 }  // namespace sf
+
+using namespace sf;
+
+extern "C" void sf_kernel_timing_enable(int enable) { g_timing.store(enable ? 1 : 0); }
+
+extern "C" void sf_kernel_timing_reset(void) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    for (auto &t : g_timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    g_timed.clear();
+}
+
+extern "C" sf_status sf_kernel_timing(const char *name, double *h_ms_total, int64_t *h_launches) {
+    if (!name || !h_ms_total || !h_launches) return fail(SF_ERR_INVALID_ARG, "sf_kernel_timing: NULL argument");
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    double tot = 0.0;
+    int64_t cnt = 0;
+    for (auto &t : g_timed) {
+        if (t.name != name) continue;
+        cudaError_t e = cudaEventSynchronize(t.b);
+        if (e != cudaSuccess) return fail(SF_ERR_CUDA, "sf_kernel_timing: %s", cudaGetErrorString(e));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        tot += ms;
+        ++cnt;
+    }
+    *h_ms_total = tot;
+    *h_launches = cnt;
+    return SF_OK;
+}
