@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--points", type=int, default=N_POINTS,
+                    help="cloud size (smaller clouds are for profiling only, not bench lines)")
+    ap.add_argument("--no-count", action="store_true",
+                    help="skip the pair-counting pass (value and roofline become null)")
     return ap.parse_args()
 
 
@@ -70,10 +74,10 @@ def dist_setup(ngpus):
     return rank, world, local
 
 
-def make_workload():
+def make_workload(n_points=N_POINTS):
     import numpy as np
     from paper_2601_20758_gb300 import synth
-    xyz = synth.cosmology_cloud(N_POINTS)
+    xyz = synth.cosmology_cloud(n_points)
     centre = synth.densest_cell_centre(xyz, 256)
     rois = synth.nested_rois(centre, N_ROI, 4.0)
     return np.ascontiguousarray(xyz), rois
@@ -202,7 +206,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
-    xyz, rois = make_workload()
+    xyz, rois = make_workload(args.points)
     n = xyz.shape[0]
     d_xyz = torch.from_numpy(xyz).cuda()
     p = L.make_params(rule=L.SF_BW_KNN, k=K_NN, scope=L.SF_SCOPE_GLOBAL)
@@ -215,10 +219,11 @@ def main():
     sels = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in rois]
 
     # algorithmic work: in-support pairs per ROI, counted once (not timed)
-    idx = L.sf_build_index(d_xyz, stream)
-    L.sf_bandwidths(idx, p, stream)
     pairs_grid, pairs_pts = [], []
-    for b in boxes:
+    if not args.no_count:
+        idx = L.sf_build_index(d_xyz, stream)
+        L.sf_bandwidths(idx, p, stream)
+    for b in ([] if args.no_count else boxes):
         gp, pp = ctypes.c_int64(0), ctypes.c_int64(0)
         dims = (ctypes.c_int32 * 3)(*DIMS)
         st = L.load().sf_count_support_pairs(idx, ctypes.byref(b), dims, L.SF_K_GAUSS3,
@@ -227,7 +232,8 @@ def main():
         L._check("sf_count_support_pairs", st)
         pairs_grid.append(gp.value)
         pairs_pts.append(pp.value)
-    L.sf_free_index(idx)
+    if not args.no_count:
+        L.sf_free_index(idx)
     pairs_step = sum(pairs_grid) + sum(pairs_pts)
 
     roi_ms = []
@@ -294,7 +300,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed_ms = float(t.item())
     ms_per_step = elapsed_ms / args.steps
-    value = pairs_step * args.steps * world / (elapsed_ms / 1e3)
+    value = pairs_step * args.steps * world / (elapsed_ms / 1e3) if pairs_step else None
 
     # ---- roofline of the dominant kernel
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
@@ -318,7 +324,9 @@ def main():
         byts = n * 32
         roof = {"kernel": dom, "bound": "hbm", "achieved": byts / (avg_ms * 1e-3) / 1e9,
                 "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    if not pairs_step and roof["bound"] == "alu":
+        roof["achieved"] = None
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] is not None else None
     roof["peak_source"] = ("FP32 lanes x 2 x max SM clock of measured peaks file"
                            if roof["bound"] == "alu" else "measured HBM copy bandwidth")
     roof["traffic"] = load_traffic(dom)
@@ -341,7 +349,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "points": n, "k": K_NN, "grid": list(DIMS),
+                "config": {"workload": WORKLOAD if n == N_POINTS else f"{n}-point variant (profiling only)",
+                           "points": n, "k": K_NN, "grid": list(DIMS),
                            "rois": N_ROI, "roi_edges": [float(hi[0] - lo[0]) for lo, hi in rois],
                            "l2": "inputs larger than L2 (256 MB sorted points, 5 x 8 MB grids)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -435,7 +444,7 @@ def run_e2e(args, L, torch, xyz, boxes, p, pairs_step, stream, world, barrier, d
         t = torch.tensor([el], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         el = float(t.item())
-    return {"value": pairs_step * args.steps * world / el, "unit": UNIT,
+    return {"value": pairs_step * args.steps * world / el if pairs_step else None, "unit": UNIT,
             "h2d_bytes_per_step": stats["h2d"], "d2h_bytes_per_step": stats["d2h"],
             "ms_per_step": 1e3 * el / args.steps}
 

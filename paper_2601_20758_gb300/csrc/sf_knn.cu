@@ -5,20 +5,24 @@
 // evaluation gives with d2 = ((dx*dx)+(dy*dy))+(dz*dz), dx = (double)x_i -
 // (double)x_j, ties broken by the smaller original index; h = (float)sqrt(d2_k).
 //
-// One warp per leaf of 32 Morton-consecutive query points:
-//  1. radius bound: the k-th smallest FP32 d2 among the points of the nearby
-//     leaves in sorted order (a per-lane histogram over [0, max]) bounds the
-//     true k-th distance from above;
-//  2. histogram pass: every point the index returns within that bound is
-//     binned by its FP32 d2 (32 bins, per lane, in shared memory); the bin
+// Persistent warps; each takes the next leaf of 32 Morton-consecutive query
+// points from an atomic counter (no warp waits for another):
+//  1. radius bound: per lane, the k-th smallest FP32 d2 among the points of
+//     the next leaves in sorted order, bracketed by three rounds of 32-bin
+//     histograms -- an upper bound of the true k-th distance;
+//  2. candidates: the index walk keeps the leaves within that radius of at
+//     least one lane's point; their points inside the warp's envelope box are
+//     compacted once into a per-warp buffer in global memory (L2-resident);
+//  3. histogram pass over the buffer: per lane, 32 bins of FP32 d2, the bin
 //     holding the k-th is found;
-//  3. band pass: points clearly below the bin are in; the few whose FP32 d2
-//     lies within a relative 2e-6 of the bin are re-evaluated in FP64 (no FMA
+//  4. band pass: points clearly below the bin are in; the few whose FP32 d2 lies
+//     within a relative 2e-6 of the bin are re-evaluated in FP64 (no FMA
 //     contraction) and ranked by (d2, original index). If a band overflows its
 //     buffer the bin is split again; at FP32 resolution (exact duplicates) the
 //     remaining members are extracted one by one.
 // FP32 d2 carries a relative error below 5 * 2^-24, so the 2e-6 margins make
-// every in/out decision outside the band exact.
+// every in/out decision outside the band exact. If a warp's candidates exceed
+// its buffer, its passes walk the index again instead (same result, slower).
 #include "sf_internal.cuh"
 
 namespace sf {
@@ -26,7 +30,8 @@ namespace sf {
 constexpr int kKnnWarps = 4;
 constexpr int kNB = 32;        // histogram bins per lane
 constexpr int kBand = 16;      // band buffer per lane
-constexpr int kCand = 256;     // cached candidate leaves per warp
+constexpr int kCand = 64;      // candidate leaves per walk batch
+constexpr int kCache = 8192;   // candidate points per warp buffer (global)
 constexpr int kKStack = 32 * kMaxLevels;
 constexpr float kDelta = 2.0e-6f;
 
@@ -34,8 +39,7 @@ struct KnnWarpSmem {
     int stack[kKStack];
     int cand[kCand];
     float4 blo[32], bhi[32];   // child boxes under test
-    float4 pts[kLeaf];
-    uint32_t ids[kLeaf];
+    float4 pts[kLeaf];         // staged candidates (x, y, z, original id bits)
     uint32_t hist[kNB][32];
     double bd[kBand][32];
     uint32_t bi[kBand][32];
@@ -45,8 +49,10 @@ struct KnnArgs {
     TreeView tv;
     const uint32_t *perm;
     int k;
-    float *h_sorted;        // out: h per sorted point
-    uint32_t *nbr_orig;     // out (nullable): [n][k] by original index
+    float *h_sorted;          // out: h per sorted point
+    uint32_t *nbr_orig;       // out (nullable): [n][k] by original index
+    float4 *cache;            // [slots][kCache] candidate buffers
+    unsigned int *next_leaf;  // work counter (zeroed before launch)
 };
 
 __device__ __forceinline__ float d2_f32(float4 a, float4 b) {
@@ -65,22 +71,24 @@ __device__ __forceinline__ bool key_less(double da, uint32_t ia, double db, uint
     return da < db || (da == db && ia < ib);
 }
 
-// Per-warp state of the candidate search: every lane holds one query point and
-// its squared search radius r2 (negative: the lane takes no part).
+// Per-warp candidate search: every lane holds one query point and the squared
+// radius r2 of its ball (negative: the lane takes no part).
 struct KnnWarp {
     const TreeView &tv;
     const uint32_t *perm;
     KnnWarpSmem &S;
+    float4 *cache;
     float4 q;
-    float r2;                   // squared radius of this lane's ball
-    float env_lo[3], env_hi[3]; // warp envelope of all balls
-    int ncand;
+    float r2;
+    float env_lo[3], env_hi[3];  // warp envelope of all balls
+    int ncache;
     bool overflow;
 
-    __device__ KnnWarp(const TreeView &t, const uint32_t *p, KnnWarpSmem &s) : tv(t), perm(p), S(s) {}
+    __device__ KnnWarp(const TreeView &t, const uint32_t *p, KnnWarpSmem &s, float4 *c)
+        : tv(t), perm(p), S(s), cache(c) {}
 
-    // Mask of the children (lane c holds child c at level cl) that lie within
-    // the ball of at least one lane. Conservative: relative slack 1e-5.
+    // Mask of the children (lane c holds child c at level cl) within the ball
+    // of at least one lane. Conservative: relative slack 1e-5.
     __device__ unsigned accept(int cl, int64_t c, bool valid) {
         const int lane = threadIdx.x & 31;
         bool pre = false;
@@ -154,66 +162,88 @@ struct KnnWarp {
         return 0;
     }
 
-    // Build the candidate leaf list once; if it does not fit, later passes walk again.
-    __device__ void collect() {
+    // Visit the envelope-filtered points of every accepted leaf, 32 at a time:
+    // chunk(n) is called with S.pts[0..n) staged (x, y, z, original id bits).
+    template <typename Chunk>
+    __device__ void walk_points(Chunk chunk) {
+        const int lane = threadIdx.x & 31;
         int sp;
-        ncand = start(sp);
-        if (sp > 0) ncand = walk(sp);
-        overflow = sp > 0;
+        int nl = start(sp);
+        while (true) {
+            if (nl == 0) {
+                if (sp == 0) break;
+                nl = walk(sp);
+                if (nl == 0) break;
+            }
+            for (int li = 0; li < nl; ++li) {
+                const int64_t j = (int64_t)S.cand[li] * kLeaf + lane;
+                bool in = false;
+                float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < tv.n) {
+                    p = __ldg(&tv.pos[j]);
+                    p.w = __uint_as_float(__ldg(&perm[j]));
+                    in = p.x >= env_lo[0] && p.x <= env_hi[0] && p.y >= env_lo[1] &&
+                         p.y <= env_hi[1] && p.z >= env_lo[2] && p.z <= env_hi[2];
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (in) S.pts[__popc(m & ((1u << lane) - 1u))] = p;
+                __syncwarp();
+                chunk(__popc(m));
+                __syncwarp();
+            }
+            nl = 0;
+        }
     }
 
-    __device__ void load_leaf(int64_t leaf) {
+    // Fill the global candidate buffer once.
+    __device__ void collect() {
         const int lane = threadIdx.x & 31;
-        const int64_t j = leaf * kLeaf + lane;
-        if (j < tv.n) {
-            S.pts[lane] = __ldg(&tv.pos[j]);
-            S.ids[lane] = __ldg(&perm[j]);
-        }
+        ncache = 0;
+        overflow = false;
+        walk_points([&](int n) {
+            if (ncache + n <= kCache) {
+                if (lane < n) cache[ncache + lane] = S.pts[lane];
+            } else {
+                overflow = true;
+            }
+            ncache += n;
+        });
         __syncwarp();
     }
 
-    // fn(point, original id, sorted index) for every point of every candidate leaf.
+    // fn(point with id bits in w) for every candidate, all lanes together.
     template <typename Fn>
     __device__ void each(Fn fn) {
-        auto leaves = [&](int n) {
-            for (int li = 0; li < n; ++li) {
-                const int64_t L = S.cand[li];
-                load_leaf(L);
-                const int64_t base = L * kLeaf;
-                const int cnt = (int)(tv.n - base < kLeaf ? tv.n - base : kLeaf);
-                for (int t = 0; t < cnt; ++t) fn(S.pts[t], S.ids[t], base + t);
+        const int lane = threadIdx.x & 31;
+        if (!overflow) {
+            for (int base = 0; base < ncache; base += 32) {
+                const int n = min(32, ncache - base);
+                if (lane < n) S.pts[lane] = cache[base + lane];
+                __syncwarp();
+                int t = 0;
+                for (; t + 2 <= n; t += 2) {
+                    const float4 a = S.pts[t], b = S.pts[t + 1];
+                    fn(a);
+                    fn(b);
+                }
+                if (t < n) fn(S.pts[t]);
                 __syncwarp();
             }
-        };
-        if (!overflow) {
-            leaves(ncand);
             return;
         }
-        int sp;
-        int n = start(sp);
-        while (true) {
-            if (n == 0) {
-                if (sp == 0) break;
-                n = walk(sp);
-                if (n == 0) break;
-            }
-            leaves(n);
-            n = 0;
-        }
+        walk_points([&](int n) {
+            for (int t = 0; t < n; ++t) fn(S.pts[t]);
+        });
     }
 };
 
-__global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    KnnWarpSmem &S = reinterpret_cast<KnnWarpSmem *>(smem_raw)[threadIdx.x >> 5];
+__device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_t leaf) {
     const int lane = threadIdx.x & 31;
     const TreeView &tv = a.tv;
-    const int64_t leaf = (int64_t)blockIdx.x * kKnnWarps + (threadIdx.x >> 5);
-    if (leaf >= tv.cnt[0]) return;
     const int k = a.k;
     const int64_t qi = leaf * kLeaf + lane;
     const bool valid = qi < tv.n;
-    KnnWarp W(tv, a.perm, S);
+    KnnWarp W(tv, a.perm, S, cache);
     W.q = valid ? __ldg(&tv.pos[qi]) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 q = W.q;
     const uint32_t qid = valid ? __ldg(&a.perm[qi]) : 0u;
@@ -222,20 +252,8 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
         for (int b = 0; b < kNB; ++b) S.hist[b][lane] = 0;
         __syncwarp();
     };
-    // bin search: smallest bin b with below + cum(hist[0..b]) >= k
-    auto bracket = [&](int below, int &b_out, int &before) {
-        int cum = below, b = 0;
-        for (; b < kNB - 1; ++b) {
-            const int c = S.hist[b][lane];
-            if (cum + c >= k) break;
-            cum += c;
-        }
-        b_out = b;
-        before = cum;
-    };
 
-    // ---- 1. radius bound: k-th smallest d2 among the leaves next in sorted order,
-    //         bracketed by three rounds of 32-bin histograms
+    // ---- 1. radius bound from the neighbouring leaves in sorted order
     const int64_t nleaf = tv.cnt[0];
     const int64_t wl = (int64_t)((k + 1 + 31) / 32) + 2;
     int64_t w0 = leaf - wl / 2, w1;
@@ -244,6 +262,19 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
     if (w1 >= nleaf) {
         w1 = nleaf - 1;
         w0 = w1 - wl + 1 < 0 ? 0 : w1 - wl + 1;
+    }
+    // first bracket: the farthest corner of the window leaves' joint box
+    float whi = 0.f;
+    {
+        float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t L = w0; L <= w1; ++L) {
+            const float4 lo = __ldg(&tv.nlo[L]), hi = __ldg(&tv.nhi[L]);
+            blo[0] = fminf(blo[0], lo.x); blo[1] = fminf(blo[1], lo.y); blo[2] = fminf(blo[2], lo.z);
+            bhi[0] = fmaxf(bhi[0], hi.x); bhi[1] = fmaxf(bhi[1], hi.y); bhi[2] = fmaxf(bhi[2], hi.z);
+        }
+        const float dx = fmaxf(q.x - blo[0], bhi[0] - q.x), dy = fmaxf(q.y - blo[1], bhi[1] - q.y),
+                    dz = fmaxf(q.z - blo[2], bhi[2] - q.z);
+        whi = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) * (1.0f + 1.0e-5f);
     }
     auto window_visit = [&](auto fn) {
         for (int64_t L = w0; L <= w1; ++L) {
@@ -255,10 +286,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
             __syncwarp();
         }
     };
-    float wlo = 0.f, whi = 0.f;
-    window_visit([&](float4 p, int64_t j) {
-        if (j != qi) whi = fmaxf(whi, d2_f32(q, p));
-    });
+    float wlo = 0.f;
     for (int round = 0; round < 3; ++round) {
         clear_hist();
         const float width = whi - wlo;
@@ -289,7 +317,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
     }
     const float T = valid ? whi * (1.0f + 4.0e-6f) + 1.0e-37f : -1.f;
 
-    // ---- 2. candidate leaves: within sqrt(T) of at least one lane's point
+    // ---- 2. candidates within sqrt(T) of at least one lane's point
     W.r2 = T;
     {
         const float r = valid ? sqrtf(T) * (1.0f + 1.0e-5f) : 0.f;
@@ -310,7 +338,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
     }
     W.collect();
 
-    // ---- 3. histogram and band passes, refined until the band fits
+    // ---- 3./4. histogram and band passes, refined until the band fits
     float lo_e = 0.f, hi_e = valid ? T : 0.f;
     bool done = !valid;
     int need = 0;
@@ -324,35 +352,45 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
         const float width = hi_e - lo_e;
         const float inv = width > 0.f ? (float)kNB / width : 0.f;
         const bool act = !done && !extract;
+        const float lo_a = act ? lo_e : INFINITY;   // inactive lanes skip cheaply
+        const float hi_a = act ? hi_e : -INFINITY;
         int below = 0;
-        W.each([&](float4 p, uint32_t, int64_t j) {
-            if (act && j != qi) {
-                const float d = d2_f32(q, p);
-                if (d < lo_e) ++below;
-                else if (d <= hi_e) S.hist[min(kNB - 1, (int)((d - lo_e) * inv))][lane] += 1;
+        W.each([&](float4 p) {
+            const float d = d2_f32(q, p);
+            if (d <= hi_a && __float_as_uint(p.w) != qid) {
+                if (d < lo_a) ++below;
+                else S.hist[min(kNB - 1, (int)((d - lo_a) * inv))][lane] += 1;
             }
         });
         __syncwarp();
         float e_lo = lo_e, e_hi = hi_e;
         if (act) {
-            int b, before;
-            bracket(below, b, before);
+            int cum = below, b = 0;
+            for (; b < kNB - 1; ++b) {
+                const int c = S.hist[b][lane];
+                if (cum + c >= k) break;
+                cum += c;
+            }
             e_lo = lo_e + (float)b * (width / (float)kNB);
             e_hi = (b == kNB - 1) ? hi_e : lo_e + (float)(b + 1) * (width / (float)kNB);
             band_lo = e_lo * (1.0f - kDelta);
             band_hi = e_hi * (1.0f + kDelta);
         }
+        const float bhi_a = act ? band_hi : -INFINITY;
         int nbelow = 0, nband = 0;
-        W.each([&](float4 p, uint32_t id, int64_t j) {
-            if (act && j != qi) {
-                const float d = d2_f32(q, p);
-                if (d < band_lo) ++nbelow;
-                else if (d <= band_hi) {
-                    if (nband < kBand) {
-                        S.bd[nband][lane] = d2_f64(q, p);
-                        S.bi[nband][lane] = id;
+        W.each([&](float4 p) {
+            const float d = d2_f32(q, p);
+            if (d <= bhi_a) {
+                const uint32_t id = __float_as_uint(p.w);
+                if (id != qid) {
+                    if (d < band_lo) ++nbelow;
+                    else {
+                        if (nband < kBand) {
+                            S.bd[nband][lane] = d2_f64(q, p);
+                            S.bi[nband][lane] = id;
+                        }
+                        ++nband;
                     }
-                    ++nband;
                 }
             }
         });
@@ -395,8 +433,9 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
             const bool act = extract && got < need;
             double best_d = INFINITY;
             uint32_t best_i = 0xffffffffu;
-            W.each([&](float4 p, uint32_t id, int64_t j) {
-                if (act && j != qi) {
+            W.each([&](float4 p) {
+                const uint32_t id = __float_as_uint(p.w);
+                if (act && id != qid) {
                     const float d = d2_f32(q, p);
                     if (d >= band_lo && d <= band_hi) {
                         const double dd = d2_f64(q, p);
@@ -426,15 +465,30 @@ __global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
     // ---- optional neighbour ids: the below set, then the band's first `need`
     if (a.nbr_orig) {
         int slot = 0;
-        W.each([&](float4 p, uint32_t id, int64_t j) {
-            if (valid && j != qi) {
-                const float d = d2_f32(q, p);
-                if (d < band_lo && slot < k) a.nbr_orig[(int64_t)qid * k + slot++] = id;
-            }
+        const float blo_a = valid ? band_lo : -INFINITY;
+        W.each([&](float4 p) {
+            const float d = d2_f32(q, p);
+            const uint32_t id = __float_as_uint(p.w);
+            if (d < blo_a && id != qid && slot < k) a.nbr_orig[(int64_t)qid * k + slot++] = id;
         });
         if (valid && !extract)
             for (int x = 0; x < need && x < kBand && slot + x < k; ++x)
                 a.nbr_orig[(int64_t)qid * k + slot + x] = S.bi[x][lane];
+    }
+}
+
+__global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    KnnWarpSmem &S = reinterpret_cast<KnnWarpSmem *>(smem_raw)[warp];
+    float4 *cache = a.cache + ((int64_t)blockIdx.x * kKnnWarps + warp) * kCache;
+    const int64_t nleaf = a.tv.cnt[0];
+    while (true) {
+        unsigned int leaf = 0;
+        if ((threadIdx.x & 31) == 0) leaf = atomicAdd(a.next_leaf, 1u);
+        leaf = __shfl_sync(0xffffffffu, leaf, 0);
+        if ((int64_t)leaf >= nleaf) break;
+        knn_leaf(a, S, cache, (int64_t)leaf);
     }
 }
 
@@ -471,9 +525,21 @@ sf_status knn_run(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_sorted,
         SF_TRY_CUDA(cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
+    int dev = 0, sms = 0, per_sm = 0;
+    SF_TRY_CUDA(cudaGetDevice(&dev));
+    SF_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SF_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn, kKnnWarps * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    // persistent: one resident wave, never more blocks than leaves need
+    const int64_t need_blocks = (idx->cnt[0] + kKnnWarps - 1) / kKnnWarps;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, need_blocks));
+    Scratch sc(s);
+    a.cache = sc.get<float4>(blocks * kKnnWarps * (int64_t)kCache);
+    a.next_leaf = sc.get<unsigned int>(1);
+    SF_TRY_SCRATCH(sc);
+    SF_TRY_CUDA(cudaMemsetAsync(a.next_leaf, 0, sizeof(unsigned int), s));
     KTimer timer("k_knn", s);
-    SF_TRY_CUDA(launch(k_knn, dim3(blocks_for(idx->cnt[0], kKnnWarps)), dim3(kKnnWarps * 32), smem,
-                       s, a));
+    SF_TRY_CUDA(launch(k_knn, dim3((unsigned)blocks), dim3(kKnnWarps * 32), smem, s, a));
     return SF_OK;
 }
 
