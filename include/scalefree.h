@@ -209,6 +209,36 @@ sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids
                     uint32_t *d_sel_ids, int64_t *h_nsel, double *h_threshold, void *stream);
 
 /*
+ * sf_kde_grid_static -- sf_kde_grid without any device memory allocation.
+ *
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot allocate device memory while they run: a real-time render or VR frame
+ * loop that reserved its device memory up front and cannot let an allocation
+ * stall or synchronise the GPU in the middle of a frame, and processes whose
+ * device memory is already owned by another allocator (a framework's caching
+ * allocator or a pool sized at start-up), where a cudaMalloc from this
+ * library would fail or fragment that memory. The caller still passes the
+ * inputs (the index) and the output buffer d_out.
+ *
+ * It computes the same grid as sf_kde_grid, with the same kernels and node
+ * coordinates, for rules SF_BW_KNN and SF_BW_FIXED (both scopes); rule
+ * SF_BW_MBE needs scratch proportional to the cloud and gives INVALID_ARG.
+ * All scratch lives in one fixed array of about 0.55 MB in device memory,
+ * which every GPU that loads the library holds until the process exits; it
+ * limits dims[k] to at most 1024 and the grid to at most 65536 tiles of
+ * 16 x 16 x 8 nodes (512^3 nodes fit); larger sizes give INVALID_ARG with a
+ * message. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call shares the one array and leaves its
+ * contents behind for the next: calls that overlap on the GPU (different
+ * streams, or different host threads, at the same time) race on it and must
+ * be serialised by the caller. h_mass as for sf_kde_grid.
+ */
+sf_status sf_kde_grid_static(sf_index *idx, const sf_box *roi, const int32_t dims[3],
+                             int32_t kernel, const sf_params *params, float *d_out,
+                             double *h_mass, void *stream);
+
+/*
  * sf_count_support_pairs -- the algorithmic work of one ROI recompute: the
  * number of (grid node, particle) pairs (h_grid_pairs, needs dims) and of
  * (ROI point, particle) pairs (h_point_pairs, DIRECT) whose kernel value is

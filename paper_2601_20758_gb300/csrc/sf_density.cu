@@ -591,6 +591,41 @@ sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
     return SF_OK;
 }
 
+// Same launch as density_grid, on node coordinates and per-tile partial sums
+// that the caller has already placed in device memory (no allocation here).
+sf_status density_grid_prealloc(sf_index *idx, const sf_box &roi, const GridSpec &g,
+                                const DensityCall &call, const float2 *d_axis,
+                                double *d_mass_part, float *d_out, double *d_mass, cudaStream_t s) {
+    GridArgs a;
+    a.e = engine_args(idx, roi, call);
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.tiles_x = (g.nx + kTileX - 1) / kTileX;
+    a.tiles_y = (g.ny + kTileY - 1) / kTileY;
+    a.tiles_z = (g.nz + kTileZ - 1) / kTileZ;
+    const int64_t tiles = (int64_t)a.tiles_x * a.tiles_y * a.tiles_z;
+    a.axis = d_axis;
+    a.out = d_out;
+    a.mass_part = d_mass_part;
+    a.pairs = nullptr;
+    cudaError_t e = (call.kernel == SF_K_EPAN)
+                        ? dispatch_grid<SF_K_EPAN>(call.bw, call.clip != 0, a, (unsigned)tiles, s)
+                        : dispatch_grid<SF_K_GAUSS3>(call.bw, call.clip != 0, a, (unsigned)tiles, s);
+    SF_TRY_CUDA(e);
+    if (d_mass) {
+        const double cell = g.s[0] * g.s[1] * g.s[2];
+        SF_TRY_CUDA(launch(k_mass_final, dim3(1), dim3(1024), 0, s, (const double *)d_mass_part,
+                           tiles, cell, d_mass));
+    }
+    return SF_OK;
+}
+
+int64_t grid_tile_count(const GridSpec &g) {
+    return (int64_t)((g.nx + kTileX - 1) / kTileX) * ((g.ny + kTileY - 1) / kTileY) *
+           ((g.nz + kTileZ - 1) / kTileZ);
+}
+
 // ===========================================================================
 // Points (DIRECT)
 // ===========================================================================
