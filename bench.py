@@ -294,6 +294,15 @@ def main():
         ms, cnt = ctypes.c_double(0), ctypes.c_int64(0)
         L._check("sf_kernel_timing", L.load().sf_kernel_timing(name.encode(), ctypes.byref(ms), ctypes.byref(cnt)))
         kern[name] = {"ms_total": ms.value, "launches": cnt.value}
+        if name in ("k_points", "k_grid") and hasattr(L.load(), "sf_kernel_timing_list"):
+            arr = (ctypes.c_double * 4096)()
+            got = ctypes.c_int64(0)
+            L._check("sf_kernel_timing_list", L.load().sf_kernel_timing_list(
+                name.encode(), arr, 4096, ctypes.byref(got)))
+            per = [arr[i] for i in range(min(got.value, 4096))]
+            # launches per step are one per ROI: average each ROI over the timed steps
+            kern[name]["per_roi_ms"] = [sum(per[r::N_ROI]) / max(1, len(per[r::N_ROI]))
+                                        for r in range(N_ROI)] if len(per) >= N_ROI else per
     L.load().sf_kernel_timing_reset()
     if world > 1:
         t = torch.tensor([elapsed_ms], device="cuda")
@@ -358,6 +367,7 @@ def main():
                                      "n": len(roi_sorted), "budget_ms": 11.1},
                 "pairs_per_step": {"grid": pairs_grid, "points": pairs_pts},
                 "kernels_ms_per_step": {k: v["ms_total"] / args.steps for k, v in kern.items()},
+                "kernels_ms_per_roi": {k: v.get("per_roi_ms") for k, v in kern.items() if "per_roi_ms" in v},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -260,6 +260,9 @@ sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t
 void sf_kernel_timing_enable(int enable);
 void sf_kernel_timing_reset(void);
 sf_status sf_kernel_timing(const char *name, double *h_ms_total, int64_t *h_launches);
+/* The individual durations (ms, launch order) of up to `cap` launches recorded
+ * under `name`; *h_count receives the number recorded (may exceed cap). */
+sf_status sf_kernel_timing_list(const char *name, double *h_ms, int64_t cap, int64_t *h_count);
 
 /* Synchronise `stream` and return (then clear) any status a kernel recorded
  * on the device for this index (TIMEOUT, DEGENERATE, EMPTY_ROI). */

@@ -192,7 +192,7 @@ struct GridArgs {
     int nx, ny, nz;
     int tiles_x, tiles_y, tiles_z;
     float *out;
-    double *mass_part;   // per tile, sum of rho (before the cell volume)
+    double *mass_part;          // per tile, sum of rho (before the cell volume)
     unsigned long long *pairs;  // counting variant: in-support (voxel, particle) pairs
 };
 
@@ -204,37 +204,50 @@ struct GridSmem {
     float4 su[kStage];           // staged (u_x, u_y, u_z, -)
     int2 sf[kStage];             // staged footprint: x0|x1<<8|y0<<16|y1<<24, z0|z1<<8
     float2 axt[kTileX + kTileY + kTileZ];  // the tile's node coordinates
+    uint8_t wlist[kGridThreads / 32][kStage];  // per warp: staged candidates touching its rows
     int stack[kStack];
     int leaves[kBatch];
     int wcnt[kGridThreads / 32];
-    int nleaves, sp_top, nstage;
+    int nleaves, sp_top, item;
     float uni[3];
     double inv_neff;
     double red[kGridThreads / 32];
 };
 
-template <int KER, int BW, bool CLIP, bool CNT>
-__global__ void __launch_bounds__(kGridThreads, 2) k_grid(GridArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    GridSmem &S = *reinterpret_cast<GridSmem *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
+struct TileGeom {
+    int gx0, gy0, gz0;
+    int nv[3];
+    float tlo[3], thi[3], sp3[3];
+};
+
+__device__ __forceinline__ void tile_origin(const GridArgs &a, int tile, int &gx0, int &gy0, int &gz0,
+                                            int nv[3]) {
     const int tix = tile % a.tiles_x, tiy = (tile / a.tiles_x) % a.tiles_y,
               tiz = tile / (a.tiles_x * a.tiles_y);
-    const int gx0 = tix * kTileX, gy0 = tiy * kTileY, gz0 = tiz * kTileZ;
-    const int nvx = min(kTileX, a.nx - gx0), nvy = min(kTileY, a.ny - gy0),
-              nvz = min(kTileZ, a.nz - gz0);
+    gx0 = tix * kTileX;
+    gy0 = tiy * kTileY;
+    gz0 = tiz * kTileZ;
+    nv[0] = min(kTileX, a.nx - gx0);
+    nv[1] = min(kTileY, a.ny - gy0);
+    nv[2] = min(kTileZ, a.nz - gz0);
+}
 
+// The tile's node coordinates and the call's parameters into shared memory.
+// Block-wide: every thread must call it (it contains a barrier).
+__device__ TileGeom tile_setup(const GridArgs &a, GridSmem &S, int tile) {
+    const int tid = threadIdx.x;
+    TileGeom g;
+    tile_origin(a, tile, g.gx0, g.gy0, g.gz0, g.nv);
     if (tid < kTileX + kTileY + kTileZ) {
         float2 v = make_float2(0.f, 0.f);
         if (tid < kTileX) {
-            if (tid < nvx) v = a.axis[gx0 + tid];
+            if (tid < g.nv[0]) v = a.axis[g.gx0 + tid];
         } else if (tid < kTileX + kTileY) {
             const int j = tid - kTileX;
-            if (j < nvy) v = a.axis[a.nx + gy0 + j];
+            if (j < g.nv[1]) v = a.axis[a.nx + g.gy0 + j];
         } else {
             const int j = tid - kTileX - kTileY;
-            if (j < nvz) v = a.axis[a.nx + a.ny + gz0 + j];
+            if (j < g.nv[2]) v = a.axis[a.nx + a.ny + g.gz0 + j];
         }
         S.axt[tid] = v;
     }
@@ -246,23 +259,217 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_grid(GridArgs a) {
         S.inv_neff = dp.inv_neff;
     }
     __syncthreads();
+    const int off[3] = {0, kTileX, kTileX + kTileY};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        g.tlo[k] = S.axt[off[k]].x;
+        g.thi[k] = S.axt[off[k] + g.nv[k] - 1].x;
+        // node spacing, for footprints (approximate; footprints are widened by 1)
+        g.sp3[k] = g.nv[k] > 1 ? (S.axt[off[k] + 1].x - S.axt[off[k]].x) : 1.f;
+    }
+    return g;
+}
 
-    // tile box (float; node_reaches adds a rounding margin)
-    float tlo[3], thi[3], sp3[3];
-    tlo[0] = S.axt[0].x;
-    thi[0] = S.axt[nvx - 1].x;
-    tlo[1] = S.axt[kTileX].x;
-    thi[1] = S.axt[kTileX + nvy - 1].x;
-    tlo[2] = S.axt[kTileX + kTileY].x;
-    thi[2] = S.axt[kTileX + kTileY + nvz - 1].x;
-    // node spacing along each axis, for footprints (approximate; footprints are widened by 1)
-    sp3[0] = nvx > 1 ? (S.axt[1].x - S.axt[0].x) : 1.f;
-    sp3[1] = nvy > 1 ? (S.axt[kTileX + 1].x - S.axt[kTileX].x) : 1.f;
-    sp3[2] = nvz > 1 ? (S.axt[kTileX + kTileY + 1].x - S.axt[kTileX + kTileY].x) : 1.f;
-    const int nv[3] = {nvx, nvy, nvz};
+// One chunk: the points of up to four candidate leaves are refined (support
+// footprint inside the tile, ROI clip), staged, tabulated per axis and added
+// into acc. Block-wide; ends with a barrier so shared memory can be reused.
+template <int KER, int BW, bool CLIP, bool CNT>
+__device__ void grid_chunk(const GridArgs &a, GridSmem &S, const TileGeom &g, const int *leaves,
+                           int nl, float acc[kTileZ], unsigned long long &npairs) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
+    // ---- load and refine up to 128 candidate points (threads 0..127)
+    bool acc_pt = false;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    float l[3] = {0.f, 0.f, 0.f};
+    int2 fp = make_int2(0, 0);
+    if (tid < kStage) {
+        const int li = tid >> 5;
+        if (li < nl) {
+            const int64_t i = (int64_t)leaves[li] * kLeaf + lane;
+            if (i < a.e.tv.n) {
+                p = __ldg(&a.e.tv.pos[i]);
+                point_ell<BW>(a.e, S.uni, i, p, l);
+                acc_pt = l[0] > 0.f && l[1] > 0.f && l[2] > 0.f;
+                if (CLIP)
+                    acc_pt = acc_pt && p.x >= a.e.blo[0] && p.x <= a.e.bhi[0] && p.y >= a.e.blo[1] &&
+                             p.y <= a.e.bhi[1] && p.z >= a.e.blo[2] && p.z <= a.e.bhi[2];
+                const float pc[3] = {p.x, p.y, p.z};
+                int f0[3], f1[3];
+                float qlb = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float R = l[k] * KDef<KER>::rmul;
+                    if (g.sp3[k] > 0.f) {
+                        const float a0 = fminf(fmaxf(ceilf((pc[k] - R - g.tlo[k]) / g.sp3[k]) - 1.f, -1.f), 64.f);
+                        const float a1 = fminf(fmaxf(floorf((pc[k] + R - g.tlo[k]) / g.sp3[k]) + 1.f, -1.f), 64.f);
+                        f0[k] = max(0, (int)a0);
+                        f1[k] = min(g.nv[k] - 1, (int)a1);
+                    } else {
+                        f0[k] = 0;
+                        f1[k] = g.nv[k] - 1;
+                    }
+                    if (f0[k] > f1[k]) acc_pt = false;
+                    float gap = fmaxf(fmaxf(g.tlo[k] - pc[k], pc[k] - g.thi[k]), 0.f);
+                    gap = fmaxf(gap - 1.0e-6f * (fabsf(g.tlo[k]) + fabsf(g.thi[k])), 0.f);
+                    const float t = gap / R;
+                    qlb += t * t;
+                }
+                if (!(qlb < 1.0f + 1.0e-5f)) acc_pt = false;
+                if (acc_pt) {
+                    fp.x = f0[0] | (f1[0] << 8) | (f0[1] << 16) | (f1[1] << 24);
+                    fp.y = f0[2] | (f1[2] << 8);
+                }
+            }
+        }
+    }
+    // ---- compact accepted points (stable: leaf order, then lane order)
+    const unsigned bal = __ballot_sync(0xffffffffu, acc_pt);
+    if (lane == 0) S.wcnt[warp] = __popc(bal);
+    __syncthreads();
+    int base = 0, ns = 0;
+#pragma unroll
+    for (int w = 0; w < kStage / 32; ++w) {
+        const int c = S.wcnt[w];
+        if (w < warp) base += c;
+        ns += c;
+    }
+    if (acc_pt) {
+        const int s = base + __popc(bal & ((1u << lane) - 1u));
+        const float c = a.e.cnorm / ((l[0] * l[1]) * l[2]);
+        S.sp[s] = make_float4(p.x, p.y, p.z, c);
+        S.su[s] = make_float4(KDef<KER>::uscale / l[0], KDef<KER>::uscale / l[1],
+                              KDef<KER>::uscale / l[2], 0.f);
+        S.sf[s] = fp;
+    }
+    __syncthreads();
+    // ---- per-warp lists: the staged candidates whose rows reach this warp's rows
+    {
+        int nw = 0;
+        for (int g0 = 0; g0 < ns; g0 += 32) {
+            const int sidx = g0 + lane;
+            bool hit = false;
+            if (sidx < ns) {
+                const int fx = S.sf[sidx].x;
+                const int y0 = (fx >> 16) & 255, y1 = (fx >> 24) & 255;
+                hit = !(warp * 2 + 1 < y0 || warp * 2 > y1);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) S.wlist[warp][nw + __popc(m & ((1u << lane) - 1u))] = (uint8_t)sidx;
+            nw += __popc(m);
+        }
+        __syncwarp();
+        if (lane == 0) S.wcnt[warp] = nw;
+    }
+    // ---- per-axis tables: the entries inside each staged point's footprint
+    for (int e = tid; e < ns * (kTileX + kTileY + kTileZ); e += kGridThreads) {
+        const int s = e / (kTileX + kTileY + kTileZ);
+        const int j = e - s * (kTileX + kTileY + kTileZ);
+        const int2 F = S.sf[s];
+        int axis, i, lo_i, hi_i;
+        if (j < kTileX) {
+            axis = 0; i = j; lo_i = F.x & 255; hi_i = (F.x >> 8) & 255;
+        } else if (j < kTileX + kTileY) {
+            axis = 1; i = j - kTileX; lo_i = (F.x >> 16) & 255; hi_i = (F.x >> 24) & 255;
+        } else {
+            axis = 2; i = j - kTileX - kTileY; lo_i = F.y & 255; hi_i = (F.y >> 8) & 255;
+        }
+        if (i < lo_i || i > hi_i) continue;  // never read by the accumulation
+        const float4 P = S.sp[s];
+        const float4 U = S.su[s];
+        const float pc = axis == 0 ? P.x : (axis == 1 ? P.y : P.z);
+        const float u = axis == 0 ? U.x : (axis == 1 ? U.y : U.z);
+        const float2 nc = S.axt[j];
+        const float d = (nc.x - pc) + nc.y;
+        const float t = d * u;
+        const float q = t * t;
+        const bool sup = q < KDef<KER>::qmax;
+        float2 v;
+        if (KER == SF_K_GAUSS3) {
+            const float w = sup ? ex2_approx(-q) : 0.f;
+            if (axis == 0) v = make_float2(w * P.w, sup ? q : kBig);
+            else if (axis == 1) v = make_float2(w, sup ? q : kBig);
+            else v = make_float2(w, sup ? KDef<KER>::qmax - q : -1.f);
+        } else {
+            if (axis < 2) v = make_float2(sup ? q : kBig, 0.f);
+            else v = make_float2(sup ? P.w * (1.0f - q) : -kBig, 0.f);
+        }
+        if (axis == 0) S.tx[s][i] = v;
+        else if (axis == 1) S.ty[s][i] = v;
+        else S.tz[s][i] = v;
+    }
+    __syncthreads();
+    // ---- accumulate: warp owns rows 2w, 2w+1; lane owns column cx
+    const int nw = S.wcnt[warp];
+    for (int li = 0; li < nw; ++li) {
+        const int s = S.wlist[warp][li];
+        const int2 F = S.sf[s];
+        const int x0 = F.x & 255, x1 = (F.x >> 8) & 255;
+        const int y0 = (F.x >> 16) & 255, y1 = (F.x >> 24) & 255;
+        const int z0 = F.y & 255, z1 = (F.y >> 8) & 255;
+        const bool in = cx >= x0 && cx <= x1 && cy >= y0 && cy <= y1;
+        // outside the footprint: no contribution (Gauss: q = BIG; Epan: q in .x = BIG)
+        float2 ex = KER == SF_K_GAUSS3 ? make_float2(0.f, kBig) : make_float2(kBig, 0.f);
+        float2 ey = ex;
+        if (in) {
+            ex = S.tx[s][cx];
+            ey = S.ty[s][cy];
+        }
+        if (KER == SF_K_GAUSS3) {
+            const float bse = ex.x * ey.x;
+            const float qij = ex.y + ey.y;
+#pragma unroll
+            for (int k = 0; k < kTileZ; ++k) {
+                if (k >= z0 && k <= z1) {
+                    const float2 ez = S.tz[s][k];
+                    if (qij < ez.y) {
+                        acc[k] = fmaf(bse, ez.x, acc[k]);
+                        if (CNT) ++npairs;
+                    }
+                }
+            }
+        } else {
+            const float b = S.sp[s].w * (ex.x + ey.x);
+#pragma unroll
+            for (int k = 0; k < kTileZ; ++k) {
+                if (k >= z0 && k <= z1) {
+                    const float t = S.tz[s][k].x - b;
+                    acc[k] += fmaxf(t, 0.f);
+                    if (CNT) npairs += (t > 0.f);
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
 
-    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, S.uni, node, tlo, thi); };
+// Fold a chunk's FP32 sums into the compensated per-voxel sums (TwoSum).
+__device__ __forceinline__ void fold(float acc[kTileZ], float sum[kTileZ], float cmp[kTileZ]) {
+#pragma unroll
+    for (int k = 0; k < kTileZ; ++k) {
+        const float t = sum[k] + acc[k];
+        const float bp = t - sum[k];
+        cmp[k] += (sum[k] - (t - bp)) + (acc[k] - bp);
+        sum[k] = t;
+        acc[k] = 0.f;
+    }
+}
 
+__device__ __forceinline__ void count_pairs_out(const GridArgs &a, unsigned long long npairs) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    if ((threadIdx.x & 31) == 0 && npairs) atomicAdd(a.pairs, npairs);
+}
+
+// Monolithic variant: one CTA walks the index for its tile and sums everything.
+template <int KER, int BW, bool CLIP, bool CNT>
+__global__ void __launch_bounds__(kGridThreads, 3) k_grid(GridArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GridSmem &S = *reinterpret_cast<GridSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    const TileGeom g = tile_setup(a, S, tile);
+    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, S.uni, node, g.tlo, g.thi); };
     const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
     unsigned long long npairs = 0;
     float acc[kTileZ], sum[kTileZ], cmp[kTileZ];
@@ -293,174 +500,23 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_grid(GridArgs a) {
         const int nl = S.nleaves;
         const bool more = S.sp_top > 0;
         if (nl == 0 && !more) break;
-
         for (int cb = 0; cb < nl; cb += kStage / kLeaf) {
-            // ---- load and refine up to 128 candidate points (threads 0..127)
-            bool acc_pt = false;
-            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-            float l[3] = {0.f, 0.f, 0.f};
-            int2 fp = make_int2(0, 0);
-            if (tid < kStage) {
-                const int li = cb + (tid >> 5);
-                if (li < nl) {
-                    const int64_t i = (int64_t)S.leaves[li] * kLeaf + lane;
-                    if (i < a.e.tv.n) {
-                        p = __ldg(&a.e.tv.pos[i]);
-                        point_ell<BW>(a.e, S.uni, i, p, l);
-                        acc_pt = l[0] > 0.f && l[1] > 0.f && l[2] > 0.f;
-                        if (CLIP)
-                            acc_pt = acc_pt && p.x >= a.e.blo[0] && p.x <= a.e.bhi[0] &&
-                                     p.y >= a.e.blo[1] && p.y <= a.e.bhi[1] &&
-                                     p.z >= a.e.blo[2] && p.z <= a.e.bhi[2];
-                        const float pc[3] = {p.x, p.y, p.z};
-                        int f0[3], f1[3];
-                        float qlb = 0.f;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float R = l[k] * KDef<KER>::rmul;
-                            if (sp3[k] > 0.f) {
-                                const float a0 = fminf(fmaxf(ceilf((pc[k] - R - tlo[k]) / sp3[k]) - 1.f, -1.f), 64.f);
-                                const float a1 = fminf(fmaxf(floorf((pc[k] + R - tlo[k]) / sp3[k]) + 1.f, -1.f), 64.f);
-                                f0[k] = max(0, (int)a0);
-                                f1[k] = min(nv[k] - 1, (int)a1);
-                            } else {
-                                f0[k] = 0;
-                                f1[k] = nv[k] - 1;
-                            }
-                            if (f0[k] > f1[k]) acc_pt = false;
-                            float gap = fmaxf(fmaxf(tlo[k] - pc[k], pc[k] - thi[k]), 0.f);
-                            gap = fmaxf(gap - 1.0e-6f * (fabsf(tlo[k]) + fabsf(thi[k])), 0.f);
-                            const float t = gap / R;
-                            qlb += t * t;
-                        }
-                        if (!(qlb < 1.0f + 1.0e-5f)) acc_pt = false;
-                        if (acc_pt) {
-                            fp.x = f0[0] | (f1[0] << 8) | (f0[1] << 16) | (f1[1] << 24);
-                            fp.y = f0[2] | (f1[2] << 8);
-                        }
-                    }
-                }
-            }
-            // ---- compact accepted points (stable: leaf order, then lane order)
-            const unsigned bal = __ballot_sync(0xffffffffu, acc_pt);
-            if (lane == 0) S.wcnt[warp] = __popc(bal);
-            __syncthreads();
-            int base = 0, tot = 0;
-#pragma unroll
-            for (int w = 0; w < kStage / 32; ++w) {
-                const int c = S.wcnt[w];
-                if (w < warp) base += c;
-                tot += c;
-            }
-            if (acc_pt) {
-                const int s = base + __popc(bal & ((1u << lane) - 1u));
-                const float c = a.e.cnorm / ((l[0] * l[1]) * l[2]);
-                S.sp[s] = make_float4(p.x, p.y, p.z, c);
-                S.su[s] = make_float4(KDef<KER>::uscale / l[0], KDef<KER>::uscale / l[1],
-                                      KDef<KER>::uscale / l[2], 0.f);
-                S.sf[s] = fp;
-            }
-            __syncthreads();
-            const int ns = tot;
-            // ---- per-axis tables: 40 entries per staged point
-            for (int e = tid; e < ns * (kTileX + kTileY + kTileZ); e += kGridThreads) {
-                const int s = e / (kTileX + kTileY + kTileZ);
-                const int j = e - s * (kTileX + kTileY + kTileZ);
-                const float4 P = S.sp[s];
-                const float4 U = S.su[s];
-                const int2 F = S.sf[s];
-                int axis, i, lo_i, hi_i;
-                float pc, u;
-                if (j < kTileX) {
-                    axis = 0; i = j; lo_i = F.x & 255; hi_i = (F.x >> 8) & 255; pc = P.x; u = U.x;
-                } else if (j < kTileX + kTileY) {
-                    axis = 1; i = j - kTileX; lo_i = (F.x >> 16) & 255; hi_i = (F.x >> 24) & 255; pc = P.y; u = U.y;
-                } else {
-                    axis = 2; i = j - kTileX - kTileY; lo_i = F.y & 255; hi_i = (F.y >> 8) & 255; pc = P.z; u = U.z;
-                }
-                const bool in = i >= lo_i && i <= hi_i;
-                const float2 nc = S.axt[j];
-                const float d = (nc.x - pc) + nc.y;
-                const float t = d * u;
-                const float q = t * t;
-                const bool sup = in && q < KDef<KER>::qmax;
-                float2 v;
-                if (KER == SF_K_GAUSS3) {
-                    const float w = sup ? ex2_approx(-q) : 0.f;
-                    if (axis == 0) v = make_float2(w * P.w, sup ? q : kBig);
-                    else if (axis == 1) v = make_float2(w, sup ? q : kBig);
-                    else v = make_float2(w, sup ? KDef<KER>::qmax - q : -1.f);
-                } else {
-                    if (axis < 2) v = make_float2(sup ? q : kBig, 0.f);
-                    else v = make_float2(sup ? P.w * (1.0f - q) : -kBig, 0.f);
-                }
-                if (axis == 0) S.tx[s][i] = v;
-                else if (axis == 1) S.ty[s][i] = v;
-                else S.tz[s][i] = v;
-            }
-            __syncthreads();
-            // ---- accumulate: warp owns rows 2w, 2w+1; lane owns column cx
-            for (int s = 0; s < ns; ++s) {
-                const int2 F = S.sf[s];
-                const int y0 = (F.x >> 16) & 255, y1 = (F.x >> 24) & 255;
-                if (warp * 2 + 1 < y0 || warp * 2 > y1) continue;
-                const int z0 = F.y & 255, z1 = (F.y >> 8) & 255;
-                const float2 ex = S.tx[s][cx];
-                const float2 ey = S.ty[s][cy];
-                if (KER == SF_K_GAUSS3) {
-                    const float base = ex.x * ey.x;
-                    const float qij = ex.y + ey.y;
-#pragma unroll
-                    for (int k = 0; k < kTileZ; ++k) {
-                        if (k >= z0 && k <= z1) {
-                            const float2 ez = S.tz[s][k];
-                            if (qij < ez.y) {
-                                acc[k] = fmaf(base, ez.x, acc[k]);
-                                if (CNT) ++npairs;
-                            }
-                        }
-                    }
-                } else {
-                    const float b = S.sp[s].w * (ex.x + ey.x);
-#pragma unroll
-                    for (int k = 0; k < kTileZ; ++k) {
-                        if (k >= z0 && k <= z1) {
-                            const float t = S.tz[s][k].x - b;
-                            acc[k] += fmaxf(t, 0.f);
-                            if (CNT) npairs += (t > 0.f);
-                        }
-                    }
-                }
-            }
-            // ---- fold the chunk into the compensated sums (TwoSum)
-#pragma unroll
-            for (int k = 0; k < kTileZ; ++k) {
-                const float t = sum[k] + acc[k];
-                const float bp = t - sum[k];
-                cmp[k] += (sum[k] - (t - bp)) + (acc[k] - bp);
-                sum[k] = t;
-                acc[k] = 0.f;
-            }
-            __syncthreads();
+            grid_chunk<KER, BW, CLIP, CNT>(a, S, g, S.leaves + cb, min(kStage / kLeaf, nl - cb), acc,
+                                           npairs);
+            fold(acc, sum, cmp);
         }
         if (!more) break;
     }
-
-    if (CNT) {
-        if (cx >= nvx || cy >= nvy) npairs = 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-        if (lane == 0 && npairs) atomicAdd(a.pairs, npairs);
-    }
+    if (CNT) count_pairs_out(a, (cx < g.nv[0] && cy < g.nv[1]) ? npairs : 0ull);
     // ---- write the tile and its mass
     double msum = 0.0;
     const double inv_neff = S.inv_neff;
-    if (cx < nvx && cy < nvy) {
-        float *o = a.out + ((int64_t)gz0 * a.ny + (gy0 + cy)) * a.nx + (gx0 + cx);
+    if (cx < g.nv[0] && cy < g.nv[1]) {
+        float *o = a.out + ((int64_t)g.gz0 * a.ny + (g.gy0 + cy)) * a.nx + (g.gx0 + cx);
         const int64_t zs = (int64_t)a.nx * a.ny;
 #pragma unroll
         for (int k = 0; k < kTileZ; ++k) {
-            if (k < nvz) {
+            if (k < g.nv[2]) {
                 const double v = ((double)sum[k] + (double)cmp[k]) * inv_neff;
                 const float fv = (float)v;
                 o[k * zs] = fv;
@@ -475,6 +531,158 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_grid(GridArgs a) {
     if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < kGridThreads / 32; ++w) t += S.red[w];
+        a.mass_part[tile] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Split pipeline: tiles over dense regions hold far more candidates than
+// others, so each tile's candidate leaves are listed first and cut into
+// balanced work items; persistent CTAs sum the items into per-item partial
+// grids, and a per-tile reduction adds the partials in item order.
+// ---------------------------------------------------------------------------
+constexpr int kWalkWarps = 8;
+
+struct WalkWarpSmem {
+    int stack[kStack];
+    int leaves[kBatch];
+};
+
+// One warp per tile: count (EMIT = false) or list (EMIT = true) its candidate leaves.
+template <int KER, int BW, bool CLIP, bool EMIT>
+__global__ void __launch_bounds__(kWalkWarps * 32) k_grid_walk(GridArgs a, int ntiles,
+                                                               uint32_t *cnt, const uint32_t *off,
+                                                               int *list) {
+    __shared__ WalkWarpSmem W[kWalkWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tile = blockIdx.x * kWalkWarps + warp;
+    if (tile >= ntiles) return;
+    WalkWarpSmem &S = W[warp];
+    int gx0, gy0, gz0, nv[3];
+    tile_origin(a, tile, gx0, gy0, gz0, nv);
+    float tlo[3], thi[3];
+    tlo[0] = a.axis[gx0].x;
+    thi[0] = a.axis[gx0 + nv[0] - 1].x;
+    tlo[1] = a.axis[a.nx + gy0].x;
+    thi[1] = a.axis[a.nx + gy0 + nv[1] - 1].x;
+    tlo[2] = a.axis[a.nx + a.ny + gz0].x;
+    thi[2] = a.axis[a.nx + a.ny + gz0 + nv[2] - 1].x;
+    float uni[3];
+    {
+        const DensityParams *dp = a.e.dp;
+        uni[0] = dp->ell_uniform[0];
+        uni[1] = dp->ell_uniform[1];
+        uni[2] = dp->ell_uniform[2];
+    }
+    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, uni, node, tlo, thi); };
+    int spv;
+    int nl = warp_walk_start(a.e.tv, test, S.stack, spv, S.leaves);
+    uint32_t total = 0;
+    const uint32_t base = EMIT ? off[tile] : 0u;
+    while (true) {
+        if (nl == 0) {
+            if (spv == 0) break;
+            nl = warp_walk(a.e.tv, test, S.stack, spv, S.leaves, kBatch);
+            if (nl == 0) break;
+        }
+        if (EMIT)
+            for (int i = lane; i < nl; i += 32) list[base + total + i] = S.leaves[i];
+        total += nl;
+        __syncwarp();
+        nl = 0;
+    }
+    if (!EMIT && lane == 0) cnt[tile] = total;
+}
+
+__global__ void k_grid_item_counts(const uint32_t *__restrict__ cnt, int ntiles, uint32_t lpw,
+                                   uint32_t *__restrict__ ic) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) ic[t] = max(1u, (cnt[t] + lpw - 1) / lpw);
+}
+
+__global__ void k_grid_items(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ off,
+                             const uint32_t *__restrict__ ic, const uint32_t *__restrict__ ioff,
+                             int ntiles, uint32_t lpw, int4 *__restrict__ items) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const uint32_t n = cnt[t], b = off[t];
+    for (uint32_t i = 0; i < ic[t]; ++i)
+        items[ioff[t] + i] = make_int4(t, (int)(b + i * lpw), (int)(b + min(n, (i + 1) * lpw)), 0);
+}
+
+template <int KER, int BW, bool CLIP, bool CNT>
+__global__ void __launch_bounds__(kGridThreads, 3)
+    k_grid_work(GridArgs a, const int4 *__restrict__ items, const uint32_t *__restrict__ n_items,
+                const int *__restrict__ list, double *__restrict__ part, unsigned int *next) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GridSmem &S = *reinterpret_cast<GridSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
+    const uint32_t nitems = *n_items;
+    unsigned long long npairs = 0;
+    while (true) {
+        if (tid == 0) S.item = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int item = S.item;
+        if ((uint32_t)item >= nitems) break;
+        const int4 it = items[item];
+        const TileGeom g = tile_setup(a, S, it.x);
+        float acc[kTileZ], sum[kTileZ], cmp[kTileZ];
+#pragma unroll
+        for (int k = 0; k < kTileZ; ++k) acc[k] = sum[k] = cmp[k] = 0.f;
+        unsigned long long np = 0;
+        for (int lb = it.y; lb < it.z; lb += kStage / kLeaf) {
+            grid_chunk<KER, BW, CLIP, CNT>(a, S, g, list + lb, min(kStage / kLeaf, it.z - lb), acc, np);
+            fold(acc, sum, cmp);
+        }
+        if (CNT && cx < g.nv[0] && cy < g.nv[1]) npairs += np;
+        double *o = part + ((int64_t)item * kGridThreads + tid) * kTileZ;
+#pragma unroll
+        for (int k = 0; k < kTileZ; ++k) o[k] = (double)sum[k] + (double)cmp[k];
+    }
+    if (CNT) count_pairs_out(a, npairs);
+}
+
+// Per tile: sum the items' partial grids in item order, scale, write, and the tile's mass.
+__global__ void __launch_bounds__(kGridThreads) k_grid_reduce(GridArgs a,
+                                                              const uint32_t *__restrict__ ic,
+                                                              const uint32_t *__restrict__ ioff,
+                                                              const double *__restrict__ part) {
+    __shared__ double red[kGridThreads / 32];
+    const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
+    int gx0, gy0, gz0, nv[3];
+    tile_origin(a, tile, gx0, gy0, gz0, nv);
+    const double inv_neff = a.e.dp->inv_neff;
+    double v[kTileZ];
+#pragma unroll
+    for (int k = 0; k < kTileZ; ++k) v[k] = 0.0;
+    const uint32_t i0 = ioff[tile], ni = ic[tile];
+    for (uint32_t i = 0; i < ni; ++i) {
+        const double *pp = part + ((int64_t)(i0 + i) * kGridThreads + tid) * kTileZ;
+#pragma unroll
+        for (int k = 0; k < kTileZ; ++k) v[k] += pp[k];
+    }
+    double msum = 0.0;
+    if (cx < nv[0] && cy < nv[1]) {
+        float *o = a.out + ((int64_t)gz0 * a.ny + (gy0 + cy)) * a.nx + (gx0 + cx);
+        const int64_t zs = (int64_t)a.nx * a.ny;
+#pragma unroll
+        for (int k = 0; k < kTileZ; ++k) {
+            if (k < nv[2]) {
+                const float fv = (float)(v[k] * inv_neff);
+                o[k * zs] = fv;
+                msum += (double)fv;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, o);
+    if (lane == 0) red[warp] = msum;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kGridThreads / 32; ++w) t += red[w];
         a.mass_part[tile] = t;
     }
 }
@@ -525,6 +733,86 @@ static cudaError_t dispatch_grid(int bw, bool clip, const GridArgs &a, unsigned 
         case BW_UNIFORM * 2 + 1: return launch_grid<KER, BW_UNIFORM, true>(a, tiles, s);
         case BW_ANISO * 2 + 0: return launch_grid<KER, BW_ANISO, false>(a, tiles, s);
         default: return launch_grid<KER, BW_ANISO, true>(a, tiles, s);
+    }
+}
+
+// The split pipeline for one (kernel, bandwidth mode, clip) combination.
+template <int KER, int BW, bool CLIP>
+static sf_status split_grid(const GridArgs &a0, int ntiles, cudaStream_t s) {
+    GridArgs a = a0;
+    Scratch sc(s);
+    uint32_t *cnt = sc.get<uint32_t>(ntiles);
+    uint32_t *off = sc.get<uint32_t>(ntiles);
+    uint32_t *tot = sc.get<uint32_t>(2);
+    SF_TRY_SCRATCH(sc);
+    const unsigned wb = blocks_for(ntiles, kWalkWarps);
+    SF_TRY_CUDA(launch(k_grid_walk<KER, BW, CLIP, false>, dim3(wb), dim3(kWalkWarps * 32), 0, s, a,
+                       ntiles, cnt, (const uint32_t *)nullptr, (int *)nullptr));
+    SF_TRY(scan_u32(cnt, off, ntiles, tot, s));
+    uint32_t total = 0;
+    SF_TRY_CUDA(cudaMemcpyAsync(&total, tot, sizeof total, cudaMemcpyDeviceToHost, s));
+    SF_TRY_CUDA(cudaStreamSynchronize(s));
+    int dev = 0, sms = 0, per_sm = 0;
+    SF_TRY_CUDA(cudaGetDevice(&dev));
+    SF_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = sizeof(GridSmem);
+    static bool attr = false;
+    if (!attr) {
+        SF_TRY_CUDA(cudaFuncSetAttribute(k_grid_work<KER, BW, CLIP, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SF_TRY_CUDA(cudaFuncSetAttribute(k_grid_work<KER, BW, CLIP, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    SF_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_work<KER, BW, CLIP, false>,
+                                                              kGridThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t slots = (int64_t)sms * per_sm;
+    // leaves per item: about four items per resident CTA, a multiple of the chunk
+    uint32_t lpw = (uint32_t)std::max<int64_t>(16, (total + 4 * slots - 1) / (4 * slots));
+    lpw = (lpw + 3) & ~3u;
+    const int64_t max_items = ntiles + total / lpw + 1;
+    int *list = sc.get<int>(std::max<int64_t>(1, total));
+    uint32_t *ic = sc.get<uint32_t>(ntiles);
+    uint32_t *ioff = sc.get<uint32_t>(ntiles);
+    int4 *items = sc.get<int4>(max_items);
+    double *part = sc.get<double>(max_items * kGridThreads * kTileZ);
+    unsigned int *next = sc.get<unsigned int>(1);
+    SF_TRY_SCRATCH(sc);
+    SF_TRY_CUDA(launch(k_grid_walk<KER, BW, CLIP, true>, dim3(wb), dim3(kWalkWarps * 32), 0, s, a,
+                       ntiles, (uint32_t *)nullptr, (const uint32_t *)off, list));
+    SF_TRY_CUDA(launch(k_grid_item_counts, dim3(blocks_for(ntiles, 256)), dim3(256), 0, s,
+                       (const uint32_t *)cnt, ntiles, lpw, ic));
+    SF_TRY(scan_u32(ic, ioff, ntiles, tot + 1, s));
+    SF_TRY_CUDA(launch(k_grid_items, dim3(blocks_for(ntiles, 256)), dim3(256), 0, s,
+                       (const uint32_t *)cnt, (const uint32_t *)off, (const uint32_t *)ic,
+                       (const uint32_t *)ioff, ntiles, lpw, items));
+    SF_TRY_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned int), s));
+    {
+        KTimer t(a.pairs ? "k_grid_work_count" : "k_grid_work", s);
+        if (a.pairs)
+            SF_TRY_CUDA(launch(k_grid_work<KER, BW, CLIP, true>, dim3((unsigned)slots), dim3(kGridThreads),
+                               smem, s, a, (const int4 *)items, (const uint32_t *)(tot + 1),
+                               (const int *)list, part, next));
+        else
+            SF_TRY_CUDA(launch(k_grid_work<KER, BW, CLIP, false>, dim3((unsigned)slots), dim3(kGridThreads),
+                               smem, s, a, (const int4 *)items, (const uint32_t *)(tot + 1),
+                               (const int *)list, part, next));
+    }
+    SF_TRY_CUDA(launch(k_grid_reduce, dim3(ntiles), dim3(kGridThreads), 0, s, a, (const uint32_t *)ic,
+                       (const uint32_t *)ioff, (const double *)part));
+    return SF_OK;
+}
+
+template <int KER>
+static sf_status dispatch_split(int bw, bool clip, const GridArgs &a, int ntiles, cudaStream_t s) {
+    switch (bw * 2 + (clip ? 1 : 0)) {
+        case BW_ISO * 2 + 0: return split_grid<KER, BW_ISO, false>(a, ntiles, s);
+        case BW_ISO * 2 + 1: return split_grid<KER, BW_ISO, true>(a, ntiles, s);
+        case BW_UNIFORM * 2 + 0: return split_grid<KER, BW_UNIFORM, false>(a, ntiles, s);
+        case BW_UNIFORM * 2 + 1: return split_grid<KER, BW_UNIFORM, true>(a, ntiles, s);
+        case BW_ANISO * 2 + 0: return split_grid<KER, BW_ANISO, false>(a, ntiles, s);
+        default: return split_grid<KER, BW_ANISO, true>(a, ntiles, s);
     }
 }
 
@@ -579,10 +867,13 @@ sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
     a.out = d_out;
     a.mass_part = mass_part;
     a.pairs = d_pairs;
-    cudaError_t e = (call.kernel == SF_K_EPAN)
-                        ? dispatch_grid<SF_K_EPAN>(call.bw, call.clip != 0, a, (unsigned)tiles, s)
-                        : dispatch_grid<SF_K_GAUSS3>(call.bw, call.clip != 0, a, (unsigned)tiles, s);
-    SF_TRY_CUDA(e);
+    {
+        KTimer t(d_pairs ? "k_grid_count" : "k_grid", s);
+        if (call.kernel == SF_K_EPAN)
+            SF_TRY(dispatch_split<SF_K_EPAN>(call.bw, call.clip != 0, a, (int)tiles, s));
+        else
+            SF_TRY(dispatch_split<SF_K_GAUSS3>(call.bw, call.clip != 0, a, (int)tiles, s));
+    }
     if (d_mass) {
         const double cell = g.s[0] * g.s[1] * g.s[2];
         SF_TRY_CUDA(launch(k_mass_final, dim3(1), dim3(1024), 0, s, (const double *)mass_part,
@@ -591,8 +882,9 @@ sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
     return SF_OK;
 }
 
-// Same launch as density_grid, on node coordinates and per-tile partial sums
-// that the caller has already placed in device memory (no allocation here).
+// Same result as density_grid with the monolithic kernel, on node coordinates
+// and per-tile partial sums that the caller has already placed in device
+// memory (no allocation here).
 sf_status density_grid_prealloc(sf_index *idx, const sf_box &roi, const GridSpec &g,
                                 const DensityCall &call, const float2 *d_axis,
                                 double *d_mass_part, float *d_out, double *d_mass, cudaStream_t s) {
@@ -693,14 +985,37 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
             nl = warp_walk(a.e.tv, test, S.stack, spv, S.leaves, kBatch);
             if (nl == 0) break;
         }
+        // software pipeline: the next candidate leaf's point is loaded one step ahead
+        float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 en = pn;
+        {
+            const int64_t j0 = (int64_t)S.leaves[0] * kLeaf + lane;
+            if (j0 < a.e.tv.n) {
+                pn = __ldg(&a.e.tv.pos[j0]);
+                if (BW == BW_ANISO) en = __ldg(&a.e.ell[j0]);
+            }
+        }
         for (int li = 0; li < nl; ++li) {
             const int64_t j = (int64_t)S.leaves[li] * kLeaf + lane;
+            const float4 p = pn;
+            const float4 pe = en;
+            if (li + 1 < nl) {
+                const int64_t jn = (int64_t)S.leaves[li + 1] * kLeaf + lane;
+                if (jn < a.e.tv.n) {
+                    pn = __ldg(&a.e.tv.pos[jn]);
+                    if (BW == BW_ANISO) en = __ldg(&a.e.ell[jn]);
+                }
+            }
             bool ok = false;
-            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
             float l[3] = {0.f, 0.f, 0.f};
             if (j < a.e.tv.n) {
-                p = __ldg(&a.e.tv.pos[j]);
-                point_ell<BW>(a.e, s_uni, j, p, l);
+                if (BW == BW_ISO) {
+                    l[0] = l[1] = l[2] = p.w;
+                } else if (BW == BW_UNIFORM) {
+                    l[0] = s_uni[0]; l[1] = s_uni[1]; l[2] = s_uni[2];
+                } else {
+                    l[0] = pe.x; l[1] = pe.y; l[2] = pe.z;
+                }
                 ok = l[0] > 0.f && l[1] > 0.f && l[2] > 0.f;
                 if (CLIP)
                     ok = ok && p.x >= a.e.blo[0] && p.x <= a.e.bhi[0] && p.y >= a.e.blo[1] &&
@@ -720,26 +1035,44 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
             if (ok) {
                 const int s = __popc(m & ((1u << lane) - 1u));
                 S.sp[s] = make_float4(p.x, p.y, p.z, a.e.cnorm / ((l[0] * l[1]) * l[2]));
-                S.su[s] = make_float4(KDef<KER>::uscale / l[0], KDef<KER>::uscale / l[1],
-                                      KDef<KER>::uscale / l[2], 0.f);
+                const float u0 = KDef<KER>::uscale / l[0];
+                if (BW == BW_ISO) {
+                    S.su[s] = make_float4(u0 * u0, 0.f, 0.f, 0.f);
+                } else {
+                    S.su[s] = make_float4(u0, KDef<KER>::uscale / l[1], KDef<KER>::uscale / l[2], 0.f);
+                }
             }
             __syncwarp();
             const int ns = __popc(m);
-            float acc = 0.f;
-            for (int s = 0; s < ns; ++s) {
+            float acc0 = 0.f, acc1 = 0.f;
+            auto pair = [&](int s, float &acc) {
                 const float4 P = S.sp[s];
-                const float4 U = S.su[s];
-                const float tx = (q.x - P.x) * U.x;
-                const float ty = (q.y - P.y) * U.y;
-                const float tz = (q.z - P.z) * U.z;
-                const float qq = fmaf(tz, tz, fmaf(ty, ty, tx * tx));
+                float qq;
+                if (BW == BW_ISO) {
+                    const float u2 = S.su[s].x;
+                    const float dx = q.x - P.x, dy = q.y - P.y, dz = q.z - P.z;
+                    qq = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) * u2;
+                } else {
+                    const float4 U = S.su[s];
+                    const float tx = (q.x - P.x) * U.x;
+                    const float ty = (q.y - P.y) * U.y;
+                    const float tz = (q.z - P.z) * U.z;
+                    qq = fmaf(tz, tz, fmaf(ty, ty, tx * tx));
+                }
                 if (qq < KDef<KER>::qmax) {
                     if (KER == SF_K_GAUSS3) acc = fmaf(P.w, ex2_approx(-qq), acc);
                     else acc = fmaf(P.w, 1.0f - qq, acc);
                     if (CNT) ++npairs;
                 }
+            };
+            int s = 0;
+            for (; s + 2 <= ns; s += 2) {
+                pair(s, acc0);
+                pair(s + 1, acc1);
             }
+            if (s < ns) pair(s, acc0);
             __syncwarp();
+            const float acc = acc0 + acc1;
             const float t = sum + acc;
             const float bp = t - sum;
             cmp += (sum - (t - bp)) + (acc - bp);

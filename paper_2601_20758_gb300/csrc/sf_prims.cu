@@ -366,6 +366,25 @@ extern "C" void sf_kernel_timing_reset(void) {
     g_timed.clear();
 }
 
+extern "C" sf_status sf_kernel_timing_list(const char *name, double *h_ms, int64_t cap,
+                                           int64_t *h_count) {
+    if (!name || !h_count || (cap > 0 && !h_ms))
+        return fail(SF_ERR_INVALID_ARG, "sf_kernel_timing_list: NULL argument");
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    int64_t cnt = 0;
+    for (auto &t : g_timed) {
+        if (t.name != name) continue;
+        cudaError_t e = cudaEventSynchronize(t.b);
+        if (e != cudaSuccess) return fail(SF_ERR_CUDA, "sf_kernel_timing_list: %s", cudaGetErrorString(e));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        if (cnt < cap) h_ms[cnt] = ms;
+        ++cnt;
+    }
+    *h_count = cnt;
+    return SF_OK;
+}
+
 extern "C" sf_status sf_kernel_timing(const char *name, double *h_ms_total, int64_t *h_launches) {
     if (!name || !h_ms_total || !h_launches) return fail(SF_ERR_INVALID_ARG, "sf_kernel_timing: NULL argument");
     std::lock_guard<std::mutex> lk(g_timing_mu);
