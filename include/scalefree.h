@@ -209,6 +209,41 @@ sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids
                     uint32_t *d_sel_ids, int64_t *h_nsel, double *h_threshold, void *stream);
 
 /*
+ * Batched ROI grids: many ROIs of uneven size in one persistent execution.
+ *
+ * Every (ROI, 16x16xZ node tile) lists its candidate leaves, the lists are cut
+ * into work items of similar size, one persistent kernel drains the items of
+ * all ROIs, and each tile adds its items' partial sums in a fixed order: a
+ * plan's results are bit-identical from run to run, and equal sf_kde_grid's up
+ * to the final rounding to float (the items are cut differently). sf_batch_create sizes the buffers (it synchronises the stream)
+ * and, unless tune->no_graph, captures the execution into a CUDA graph that
+ * sf_batch_run replays; the index must not change while a batch exists.
+ * Rules KNN and FIXED, both scopes (CLIP counts N_B per ROI at creation).
+ *
+ * rois: nroi closed boxes; dims: nroi x 3 int32 (dims[3r..3r+2] for ROI r,
+ * each in [2, 4096]). d_outs: nroi device pointers, grid r of
+ * dims[3r+2]*dims[3r+1]*dims[3r] floats, x fastest (may change between runs).
+ * h_masses (nullable, host double[nroi]): FP64 mass per ROI; synchronises.
+ */
+typedef struct sf_batch sf_batch;
+typedef struct {
+    int32_t tile_z;          /* node tile depth in z: 4 or 8 (0: 8)                 */
+    int32_t items_per_slot;  /* work items per resident CTA, 1..64 (0: 4)           */
+    int32_t no_graph;        /* 1: launch the kernels directly instead of a graph   */
+    int32_t reserved;        /* must be 0                                           */
+} sf_tune;
+
+sf_status sf_batch_create(sf_index *idx, int32_t nroi, const sf_box *rois, const int32_t *dims,
+                          int32_t kernel, const sf_params *params, const sf_tune *tune,
+                          void *stream, sf_batch **out);
+sf_status sf_batch_run(sf_batch *batch, float *const *d_outs, double *h_masses, void *stream);
+void sf_batch_free(sf_batch *batch);
+/* One-shot: create (without a graph), run, free. */
+sf_status sf_batch_kde_grid(sf_index *idx, int32_t nroi, const sf_box *rois, const int32_t *dims,
+                            int32_t kernel, const sf_params *params, float *const *d_outs,
+                            double *h_masses, void *stream);
+
+/*
  * sf_kde_grid_static -- sf_kde_grid without any device memory allocation.
  *
  * The paper has no counterpart; this entry point exists for callers that

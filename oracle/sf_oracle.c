@@ -120,8 +120,9 @@ int or_knn(const float *xyz, int64_t n, int k, const int64_t *q, int64_t nq,
  *
  * member (nullable): n flags; 0 excludes particle j (the ROI clip scope).
  * wpeak (nullable): inv_neff * sum over in-support j of K(0; l_j).
- * amb   (nullable): inv_neff * sum of K over pairs with |q/qmax - 1| < 1e-6,
- *                   the mass whose in/out decision depends on rounding.
+ * amb   (nullable): inv_neff * sum of |K| (untruncated profile) over pairs with
+ *                   |q/qmax - 1| < 1e-6 on either side of the cutoff: the mass
+ *                   whose in/out decision depends on rounding order alone.
  * pairs (nullable): number of in-support (q < qmax) pairs per target.
  */
 void or_density_at(const float *xyz, int64_t n, const double *ell,
@@ -146,12 +147,16 @@ void or_density_at(const float *xyz, int64_t n, const double *ell,
             double uy = (ry - (double)xyz[3 * j + 1]) / ly;
             double uz = (rz - (double)xyz[3 * j + 2]) / lz;
             double qq = ((ux * ux) + (uy * uy)) + (uz * uz);
-            if (!(qq < qmax)) continue;
+            /* pairs this close to the cutoff are in or out by rounding order alone:
+               their kernel value counts as ambiguous on both sides of q = qmax */
+            int ambiguous = fabs(qq / qmax - 1.0) < 1e-6;
+            if (!(qq < qmax) && !ambiguous) continue;
             double peak = cnorm / ((lx * ly) * lz);
             double val = (kernel == OR_K_EPAN) ? peak * (1.0 - qq) : peak * exp(-0.5 * qq);
+            if (ambiguous) asum += fabs(val);
+            if (!(qq < qmax)) continue;
             sum += val;
             wsum += peak;
-            if (fabs(qq / qmax - 1.0) < 1e-6) asum += val;
             ++np;
         }
         rho[t] = inv_neff * sum;

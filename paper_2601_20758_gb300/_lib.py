@@ -54,6 +54,11 @@ class sf_params(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class sf_tune(ctypes.Structure):
+    _fields_ = [("tile_z", ctypes.c_int32), ("items_per_slot", ctypes.c_int32),
+                ("no_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class SFError(RuntimeError):
     def __init__(self, fn, status, msg):
         super().__init__(f"{fn}: {STATUS_NAMES.get(status, status)}: {msg}")
@@ -76,6 +81,24 @@ _PROTOS = {
     "sf_select": (ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _vp, _vp,
                                  ctypes.POINTER(_i64), ctypes.POINTER(_dbl), _vp]),
     "sf_sync_status": (ctypes.c_int, [_vp, _vp]),
+    "sf_batch_create": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
+                                       ctypes.POINTER(sf_params), ctypes.POINTER(sf_tune), _vp,
+                                       ctypes.POINTER(_vp)]),
+    "sf_batch_run": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_dbl), _vp]),
+    "sf_batch_free": (None, [_vp]),
+    "sf_batch_kde_grid": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
+                                         ctypes.POINTER(sf_params), ctypes.POINTER(_vp),
+                                         ctypes.POINTER(_dbl), _vp]),
+    "sf_count_support_pairs": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
+                                              ctypes.POINTER(sf_params), ctypes.POINTER(_i64),
+                                              ctypes.POINTER(_i64), _vp]),
+    "sf_kde_grid_static": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
+                                          ctypes.POINTER(sf_params), _vp, ctypes.POINTER(_dbl), _vp]),
+    "sf_kernel_timing_enable": (None, [ctypes.c_int]),
+    "sf_kernel_timing_reset": (None, []),
+    "sf_kernel_timing": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
+    "sf_kernel_timing_list": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_dbl), _i64,
+                                             ctypes.POINTER(_i64)]),
     "sf_free_index": (None, [_vp]),
     "sf_last_error": (ctypes.c_char_p, []),
     "sf_launch_count": (ctypes.c_uint64, []),
@@ -198,6 +221,45 @@ def sf_select(idx, d_density, d_ids, n, n_total, threshold=math.nan, percentile=
         None if d_sel_ids is None else d_sel_ids.data_ptr(), ctypes.byref(ns), ctypes.byref(t),
         _stream(stream)))
     return int(ns.value), float(t.value)
+
+
+def _boxes_dims(boxes, dims_list):
+    n = len(boxes)
+    arr = (sf_box * n)(*boxes)
+    d = (_i32 * (3 * n))(*[int(v) for dd in dims_list for v in dd])
+    return n, arr, d
+
+
+def sf_batch_create(idx, boxes, dims_list, kernel, params, tune=None, stream=None):
+    """Plan a batch of ROI grids (boxes: list of sf_box, dims_list: list of (nx, ny, nz))."""
+    n, arr, d = _boxes_dims(boxes, dims_list)
+    h = _vp()
+    _check("sf_batch_create", load().sf_batch_create(idx, n, arr, d, int(kernel), ctypes.byref(params),
+                                                     None if tune is None else ctypes.byref(tune),
+                                                     _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def sf_batch_run(batch, outs, want_mass=False, stream=None):
+    n = len(outs)
+    ptrs = (_vp * n)(*[o.data_ptr() for o in outs])
+    m = (_dbl * n)()
+    _check("sf_batch_run", load().sf_batch_run(batch, ptrs, m if want_mass else None, _stream(stream)))
+    return list(m) if want_mass else None
+
+
+def sf_batch_free(batch):
+    load().sf_batch_free(batch)
+
+
+def sf_batch_kde_grid(idx, boxes, dims_list, kernel, params, outs, want_mass=False, stream=None):
+    n, arr, d = _boxes_dims(boxes, dims_list)
+    ptrs = (_vp * n)(*[o.data_ptr() for o in outs])
+    m = (_dbl * n)()
+    _check("sf_batch_kde_grid", load().sf_batch_kde_grid(idx, n, arr, d, int(kernel), ctypes.byref(params),
+                                                         ptrs, m if want_mass else None,
+                                                         _stream(stream)))
+    return list(m) if want_mass else None
 
 
 def sf_sync_status(idx, stream=None) -> int:

@@ -348,6 +348,90 @@ sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t
     return sf_sync_status(idx, stream);
 }
 
+struct sf_batch {
+    sf::BatchPlan *plan = nullptr;
+    int nroi = 0;
+};
+
+sf_status sf_batch_create(sf_index *idx, int32_t nroi, const sf_box *rois, const int32_t *dims,
+                          int32_t kernel, const sf_params *params, const sf_tune *tune,
+                          void *stream, sf_batch **out) {
+    clear_error();
+    if (!out) return fail(SF_ERR_INVALID_ARG, "sf_batch_create: out is NULL");
+    *out = nullptr;
+    if (!idx || !rois || !dims || nroi < 1 || nroi > 65536)
+        return fail(SF_ERR_INVALID_ARG, "sf_batch_create: bad arguments (nroi=%d)", nroi);
+    SF_TRY(check_params(idx, params, kernel, "sf_batch_create"));
+    if (params->rule == SF_BW_MBE)
+        return fail(SF_ERR_INVALID_ARG, "sf_batch_create: rule MBE is per ROI; use sf_kde_grid");
+    int tz = 8, ips = 4;
+    bool graph = true;
+    if (tune) {
+        if (tune->tile_z != 0 && tune->tile_z != 4 && tune->tile_z != 8)
+            return fail(SF_ERR_INVALID_ARG, "sf_batch_create: tile_z must be 4 or 8");
+        if (tune->tile_z) tz = tune->tile_z;
+        if (tune->items_per_slot < 0 || tune->items_per_slot > 64)
+            return fail(SF_ERR_INVALID_ARG, "sf_batch_create: items_per_slot outside [0, 64]");
+        if (tune->items_per_slot) ips = tune->items_per_slot;
+        graph = tune->no_graph == 0;
+    }
+    std::vector<GridSpec> grids(nroi);
+    for (int r = 0; r < nroi; ++r) {
+        SF_TRY(check_roi(&rois[r], "sf_batch_create"));
+        SF_TRY(make_grid(rois[r], dims + 3 * r, grids[r], "sf_batch_create"));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    DensityParams *dps = nullptr;
+    SF_TRY_CUDA(cudaMalloc(&dps, sizeof(DensityParams) * nroi));
+    const bool clip = params->scope == SF_SCOPE_CLIP;
+    float ell[3] = {0.f, 0.f, 0.f};
+    const int bw = params->rule == SF_BW_FIXED ? BW_UNIFORM : BW_ISO;
+    if (bw == BW_UNIFORM)
+        for (int k = 0; k < 3; ++k) ell[k] = (float)params->fixed_h[k];
+    for (int r = 0; r < nroi; ++r) {
+        sf_status st = set_density_params(idx, clip, rois[r], ell, dps + r, s);
+        if (st != SF_OK) {
+            cudaFree(dps);
+            return st;
+        }
+    }
+    sf::BatchPlan *plan = nullptr;
+    SF_TRY(batch_create(idx, nroi, rois, grids.data(), kernel, bw, clip, dps, tz, ips, graph, s, &plan));
+    sf_batch *b = new sf_batch();
+    b->plan = plan;
+    b->nroi = nroi;
+    *out = b;
+    return sf_sync_status(idx, stream);
+}
+
+sf_status sf_batch_run(sf_batch *b, float *const *d_outs, double *h_masses, void *stream) {
+    clear_error();
+    if (!b || !d_outs) return fail(SF_ERR_INVALID_ARG, "sf_batch_run: NULL argument");
+    for (int r = 0; r < b->nroi; ++r)
+        if (!d_outs[r]) return fail(SF_ERR_INVALID_ARG, "sf_batch_run: output %d is NULL", r);
+    return batch_run(b->plan, d_outs, h_masses, (cudaStream_t)stream);
+}
+
+void sf_batch_free(sf_batch *b) {
+    if (!b) return;
+    batch_free(b->plan);
+    delete b;
+}
+
+sf_status sf_batch_kde_grid(sf_index *idx, int32_t nroi, const sf_box *rois, const int32_t *dims,
+                            int32_t kernel, const sf_params *params, float *const *d_outs,
+                            double *h_masses, void *stream) {
+    sf_tune t;
+    memset(&t, 0, sizeof t);
+    t.no_graph = 1;  // a one-shot batch gains nothing from a graph
+    sf_batch *b = nullptr;
+    SF_TRY(sf_batch_create(idx, nroi, rois, dims, kernel, params, &t, stream, &b));
+    sf_status st = sf_batch_run(b, d_outs, h_masses, stream);
+    if (st == SF_OK) st = sf_sync_status(idx, stream);
+    sf_batch_free(b);
+    return st;
+}
+
 sf_status sf_sync_status(sf_index *idx, void *stream) {
     if (!idx) return fail(SF_ERR_INVALID_ARG, "sf_sync_status: NULL index");
     cudaStream_t s = (cudaStream_t)stream;

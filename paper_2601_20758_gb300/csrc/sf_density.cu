@@ -186,24 +186,27 @@ __device__ __forceinline__ void point_ell(const EngineArgs &a, const float *uni,
 // ===========================================================================
 // Grid
 // ===========================================================================
-struct GridArgs {
-    EngineArgs e;
+// Geometry and outputs of one ROI grid (device-side descriptor).
+struct RoiDesc {
     const float2 *axis;  // node coordinates as (hi, lo) float pairs: x[nx], y[ny], z[nz]
     int nx, ny, nz;
     int tiles_x, tiles_y, tiles_z;
-    float *out;
-    double *mass_part;          // per tile, sum of rho (before the cell volume)
-    unsigned long long *pairs;  // counting variant: in-support (voxel, particle) pairs
+    int tile_base;       // first global tile index of this ROI
+    float *out;          // dims[2] x dims[1] x dims[0], x fastest
+    double *mass_part;   // per tile of this ROI
+    const DensityParams *dp;
+    float blo[3], bhi[3];  // clip box (float bounds of the closed double box)
 };
 
-struct GridSmem {
+template <int TZ>
+struct GridSmemT {
     float2 tx[kStage][kTileX];   // Gauss: (c e^{-qx'}, qx'); Epan: (qx', -)
     float2 ty[kStage][kTileY];   // Gauss: (e^{-qy'}, qy');   Epan: (qy', -)
-    float2 tz[kStage][kTileZ];   // Gauss: (e^{-qz'}, qmax - qz'); Epan: (c (1 - qz'), -)
+    float2 tz[kStage][TZ];       // Gauss: (e^{-qz'}, qmax - qz'); Epan: (c (1 - qz'), -)
     float4 sp[kStage];           // staged (x, y, z, c)
     float4 su[kStage];           // staged (u_x, u_y, u_z, -)
     int2 sf[kStage];             // staged footprint: x0|x1<<8|y0<<16|y1<<24, z0|z1<<8
-    float2 axt[kTileX + kTileY + kTileZ];  // the tile's node coordinates
+    float2 axt[kTileX + kTileY + TZ];  // the tile's node coordinates
     uint8_t wlist[kGridThreads / 32][kStage];  // per warp: staged candidates touching its rows
     int stack[kStack];
     int leaves[kBatch];
@@ -212,6 +215,8 @@ struct GridSmem {
     float uni[3];
     double inv_neff;
     double red[kGridThreads / 32];
+    EngineArgs e;                // the call's engine arguments with this ROI's clip box and params
+    RoiDesc roi;
 };
 
 struct TileGeom {
@@ -220,39 +225,42 @@ struct TileGeom {
     float tlo[3], thi[3], sp3[3];
 };
 
-__device__ __forceinline__ void tile_origin(const GridArgs &a, int tile, int &gx0, int &gy0, int &gz0,
+template <int TZ>
+__device__ __forceinline__ void tile_origin(const RoiDesc &r, int tile, int &gx0, int &gy0, int &gz0,
                                             int nv[3]) {
-    const int tix = tile % a.tiles_x, tiy = (tile / a.tiles_x) % a.tiles_y,
-              tiz = tile / (a.tiles_x * a.tiles_y);
+    const int tix = tile % r.tiles_x, tiy = (tile / r.tiles_x) % r.tiles_y,
+              tiz = tile / (r.tiles_x * r.tiles_y);
     gx0 = tix * kTileX;
     gy0 = tiy * kTileY;
-    gz0 = tiz * kTileZ;
-    nv[0] = min(kTileX, a.nx - gx0);
-    nv[1] = min(kTileY, a.ny - gy0);
-    nv[2] = min(kTileZ, a.nz - gz0);
+    gz0 = tiz * TZ;
+    nv[0] = min(kTileX, r.nx - gx0);
+    nv[1] = min(kTileY, r.ny - gy0);
+    nv[2] = min(TZ, r.nz - gz0);
 }
 
-// The tile's node coordinates and the call's parameters into shared memory.
-// Block-wide: every thread must call it (it contains a barrier).
-__device__ TileGeom tile_setup(const GridArgs &a, GridSmem &S, int tile) {
+// The tile's node coordinates and the call's parameters into shared memory
+// (S.roi and S.e must be set). Block-wide: it contains a barrier.
+template <int TZ>
+__device__ TileGeom tile_setup(GridSmemT<TZ> &S, int tile) {
     const int tid = threadIdx.x;
+    const RoiDesc &r = S.roi;
     TileGeom g;
-    tile_origin(a, tile, g.gx0, g.gy0, g.gz0, g.nv);
-    if (tid < kTileX + kTileY + kTileZ) {
+    tile_origin<TZ>(r, tile, g.gx0, g.gy0, g.gz0, g.nv);
+    if (tid < kTileX + kTileY + TZ) {
         float2 v = make_float2(0.f, 0.f);
         if (tid < kTileX) {
-            if (tid < g.nv[0]) v = a.axis[g.gx0 + tid];
+            if (tid < g.nv[0]) v = r.axis[g.gx0 + tid];
         } else if (tid < kTileX + kTileY) {
             const int j = tid - kTileX;
-            if (j < g.nv[1]) v = a.axis[a.nx + g.gy0 + j];
+            if (j < g.nv[1]) v = r.axis[r.nx + g.gy0 + j];
         } else {
             const int j = tid - kTileX - kTileY;
-            if (j < g.nv[2]) v = a.axis[a.nx + a.ny + g.gz0 + j];
+            if (j < g.nv[2]) v = r.axis[r.nx + r.ny + g.gz0 + j];
         }
         S.axt[tid] = v;
     }
     if (tid == 0) {
-        const DensityParams dp = *a.e.dp;
+        const DensityParams dp = *S.e.dp;
         S.uni[0] = dp.ell_uniform[0];
         S.uni[1] = dp.ell_uniform[1];
         S.uni[2] = dp.ell_uniform[2];
@@ -273,9 +281,10 @@ __device__ TileGeom tile_setup(const GridArgs &a, GridSmem &S, int tile) {
 // One chunk: the points of up to four candidate leaves are refined (support
 // footprint inside the tile, ROI clip), staged, tabulated per axis and added
 // into acc. Block-wide; ends with a barrier so shared memory can be reused.
-template <int KER, int BW, bool CLIP, bool CNT>
-__device__ void grid_chunk(const GridArgs &a, GridSmem &S, const TileGeom &g, const int *leaves,
-                           int nl, float acc[kTileZ], unsigned long long &npairs) {
+template <int KER, int BW, bool CLIP, bool CNT, int TZ>
+__device__ void grid_chunk(GridSmemT<TZ> &S, const TileGeom &g, const int *leaves, int nl,
+                           float acc[TZ], unsigned long long &npairs) {
+    const EngineArgs &E = S.e;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
     // ---- load and refine up to 128 candidate points (threads 0..127)
@@ -287,13 +296,13 @@ __device__ void grid_chunk(const GridArgs &a, GridSmem &S, const TileGeom &g, co
         const int li = tid >> 5;
         if (li < nl) {
             const int64_t i = (int64_t)leaves[li] * kLeaf + lane;
-            if (i < a.e.tv.n) {
-                p = __ldg(&a.e.tv.pos[i]);
-                point_ell<BW>(a.e, S.uni, i, p, l);
+            if (i < E.tv.n) {
+                p = __ldg(&E.tv.pos[i]);
+                point_ell<BW>(E, S.uni, i, p, l);
                 acc_pt = l[0] > 0.f && l[1] > 0.f && l[2] > 0.f;
                 if (CLIP)
-                    acc_pt = acc_pt && p.x >= a.e.blo[0] && p.x <= a.e.bhi[0] && p.y >= a.e.blo[1] &&
-                             p.y <= a.e.bhi[1] && p.z >= a.e.blo[2] && p.z <= a.e.bhi[2];
+                    acc_pt = acc_pt && p.x >= E.blo[0] && p.x <= E.bhi[0] && p.y >= E.blo[1] &&
+                             p.y <= E.bhi[1] && p.z >= E.blo[2] && p.z <= E.bhi[2];
                 const float pc[3] = {p.x, p.y, p.z};
                 int f0[3], f1[3];
                 float qlb = 0.f;
@@ -336,7 +345,7 @@ __device__ void grid_chunk(const GridArgs &a, GridSmem &S, const TileGeom &g, co
     }
     if (acc_pt) {
         const int s = base + __popc(bal & ((1u << lane) - 1u));
-        const float c = a.e.cnorm / ((l[0] * l[1]) * l[2]);
+        const float c = E.cnorm / ((l[0] * l[1]) * l[2]);
         S.sp[s] = make_float4(p.x, p.y, p.z, c);
         S.su[s] = make_float4(KDef<KER>::uscale / l[0], KDef<KER>::uscale / l[1],
                               KDef<KER>::uscale / l[2], 0.f);
@@ -362,9 +371,10 @@ __device__ void grid_chunk(const GridArgs &a, GridSmem &S, const TileGeom &g, co
         if (lane == 0) S.wcnt[warp] = nw;
     }
     // ---- per-axis tables: the entries inside each staged point's footprint
-    for (int e = tid; e < ns * (kTileX + kTileY + kTileZ); e += kGridThreads) {
-        const int s = e / (kTileX + kTileY + kTileZ);
-        const int j = e - s * (kTileX + kTileY + kTileZ);
+    constexpr int kEnt = kTileX + kTileY + TZ;
+    for (int e = tid; e < ns * kEnt; e += kGridThreads) {
+        const int s = e / kEnt;
+        const int j = e - s * kEnt;
         const int2 F = S.sf[s];
         int axis, i, lo_i, hi_i;
         if (j < kTileX) {
@@ -419,7 +429,7 @@ __device__ void grid_chunk(const GridArgs &a, GridSmem &S, const TileGeom &g, co
             const float bse = ex.x * ey.x;
             const float qij = ex.y + ey.y;
 #pragma unroll
-            for (int k = 0; k < kTileZ; ++k) {
+            for (int k = 0; k < TZ; ++k) {
                 if (k >= z0 && k <= z1) {
                     const float2 ez = S.tz[s][k];
                     if (qij < ez.y) {
@@ -431,7 +441,7 @@ __device__ void grid_chunk(const GridArgs &a, GridSmem &S, const TileGeom &g, co
         } else {
             const float b = S.sp[s].w * (ex.x + ey.x);
 #pragma unroll
-            for (int k = 0; k < kTileZ; ++k) {
+            for (int k = 0; k < TZ; ++k) {
                 if (k >= z0 && k <= z1) {
                     const float t = S.tz[s][k].x - b;
                     acc[k] += fmaxf(t, 0.f);
@@ -444,9 +454,10 @@ __device__ void grid_chunk(const GridArgs &a, GridSmem &S, const TileGeom &g, co
 }
 
 // Fold a chunk's FP32 sums into the compensated per-voxel sums (TwoSum).
-__device__ __forceinline__ void fold(float acc[kTileZ], float sum[kTileZ], float cmp[kTileZ]) {
+template <int TZ>
+__device__ __forceinline__ void fold(float acc[TZ], float sum[TZ], float cmp[TZ]) {
 #pragma unroll
-    for (int k = 0; k < kTileZ; ++k) {
+    for (int k = 0; k < TZ; ++k) {
         const float t = sum[k] + acc[k];
         const float bp = t - sum[k];
         cmp[k] += (sum[k] - (t - bp)) + (acc[k] - bp);
@@ -455,30 +466,56 @@ __device__ __forceinline__ void fold(float acc[kTileZ], float sum[kTileZ], float
     }
 }
 
-__device__ __forceinline__ void count_pairs_out(const GridArgs &a, unsigned long long npairs) {
+__device__ __forceinline__ void count_pairs_out(unsigned long long *dst, unsigned long long npairs) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-    if ((threadIdx.x & 31) == 0 && npairs) atomicAdd(a.pairs, npairs);
+    if ((threadIdx.x & 31) == 0 && npairs) atomicAdd(dst, npairs);
 }
 
-// Monolithic variant: one CTA walks the index for its tile and sums everything.
+// EngineArgs of one ROI: the call's common arguments with the ROI's params and clip box.
+__device__ __forceinline__ void set_roi_engine(EngineArgs &e, const EngineArgs &common, const RoiDesc &r) {
+    e = common;
+    e.dp = r.dp;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e.blo[k] = r.blo[k];
+        e.bhi[k] = r.bhi[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Monolithic variant (used by the allocation-free entry point): one CTA per
+// tile walks the index for its tile and sums everything, 8 nodes deep in z.
+// ---------------------------------------------------------------------------
+struct GridArgs {
+    EngineArgs e;
+    RoiDesc roi;
+    unsigned long long *pairs;
+};
+
 template <int KER, int BW, bool CLIP, bool CNT>
 __global__ void __launch_bounds__(kGridThreads, 3) k_grid(GridArgs a) {
+    constexpr int TZ = kTileZ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GridSmem &S = *reinterpret_cast<GridSmem *>(smem_raw);
+    GridSmemT<TZ> &S = *reinterpret_cast<GridSmemT<TZ> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
-    const TileGeom g = tile_setup(a, S, tile);
-    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, S.uni, node, g.tlo, g.thi); };
+    if (tid == 0) {
+        S.e = a.e;
+        S.roi = a.roi;
+    }
+    __syncthreads();
+    const TileGeom g = tile_setup<TZ>(S, tile);
+    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(S.e, S.uni, node, g.tlo, g.thi); };
     const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
     unsigned long long npairs = 0;
-    float acc[kTileZ], sum[kTileZ], cmp[kTileZ];
+    float acc[TZ], sum[TZ], cmp[TZ];
 #pragma unroll
-    for (int k = 0; k < kTileZ; ++k) acc[k] = sum[k] = cmp[k] = 0.f;
+    for (int k = 0; k < TZ; ++k) acc[k] = sum[k] = cmp[k] = 0.f;
 
     if (warp == 0) {
         int spv;
-        int n0 = warp_walk_start(a.e.tv, test, S.stack, spv, S.leaves);
+        int n0 = warp_walk_start(S.e.tv, test, S.stack, spv, S.leaves);
         if (lane == 0) {
             S.sp_top = spv;
             S.nleaves = n0;
@@ -489,7 +526,7 @@ __global__ void __launch_bounds__(kGridThreads, 3) k_grid(GridArgs a) {
     while (true) {
         if (warp == 0 && !(first && S.nleaves > 0)) {
             int spv = S.sp_top;
-            int n = warp_walk(a.e.tv, test, S.stack, spv, S.leaves, kBatch);
+            int n = warp_walk(S.e.tv, test, S.stack, spv, S.leaves, kBatch);
             if (lane == 0) {
                 S.sp_top = spv;
                 S.nleaves = n;
@@ -501,21 +538,22 @@ __global__ void __launch_bounds__(kGridThreads, 3) k_grid(GridArgs a) {
         const bool more = S.sp_top > 0;
         if (nl == 0 && !more) break;
         for (int cb = 0; cb < nl; cb += kStage / kLeaf) {
-            grid_chunk<KER, BW, CLIP, CNT>(a, S, g, S.leaves + cb, min(kStage / kLeaf, nl - cb), acc,
-                                           npairs);
-            fold(acc, sum, cmp);
+            grid_chunk<KER, BW, CLIP, CNT, TZ>(S, g, S.leaves + cb, min(kStage / kLeaf, nl - cb), acc,
+                                               npairs);
+            fold<TZ>(acc, sum, cmp);
         }
         if (!more) break;
     }
-    if (CNT) count_pairs_out(a, (cx < g.nv[0] && cy < g.nv[1]) ? npairs : 0ull);
+    if (CNT) count_pairs_out(a.pairs, (cx < g.nv[0] && cy < g.nv[1]) ? npairs : 0ull);
     // ---- write the tile and its mass
     double msum = 0.0;
     const double inv_neff = S.inv_neff;
+    const RoiDesc &r = S.roi;
     if (cx < g.nv[0] && cy < g.nv[1]) {
-        float *o = a.out + ((int64_t)g.gz0 * a.ny + (g.gy0 + cy)) * a.nx + (g.gx0 + cx);
-        const int64_t zs = (int64_t)a.nx * a.ny;
+        float *o = r.out + ((int64_t)g.gz0 * r.ny + (g.gy0 + cy)) * r.nx + (g.gx0 + cx);
+        const int64_t zs = (int64_t)r.nx * r.ny;
 #pragma unroll
-        for (int k = 0; k < kTileZ; ++k) {
+        for (int k = 0; k < TZ; ++k) {
             if (k < g.nv[2]) {
                 const double v = ((double)sum[k] + (double)cmp[k]) * inv_neff;
                 const float fv = (float)v;
@@ -531,58 +569,64 @@ __global__ void __launch_bounds__(kGridThreads, 3) k_grid(GridArgs a) {
     if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < kGridThreads / 32; ++w) t += S.red[w];
-        a.mass_part[tile] = t;
+        r.mass_part[tile] = t;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Split pipeline: tiles over dense regions hold far more candidates than
-// others, so each tile's candidate leaves are listed first and cut into
-// balanced work items; persistent CTAs sum the items into per-item partial
-// grids, and a per-tile reduction adds the partials in item order.
+// Split pipeline over one or many ROIs. Tiles over dense regions hold far more
+// candidates than others, so each (ROI, tile)'s candidate leaves are listed
+// first and cut into balanced work items; persistent CTAs sum the items into
+// per-item partial grids, and a per-tile reduction adds the partials in item
+// order (deterministic). Global tile index = roi.tile_base + local tile.
 // ---------------------------------------------------------------------------
+struct MrArgs {
+    EngineArgs e;               // common part (index, bandwidths, kernel constant)
+    const RoiDesc *rois;        // device array
+    const int *tile_roi;        // global tile -> ROI index
+    int ntiles;
+    unsigned long long *pairs;  // counting variant
+};
+
 constexpr int kWalkWarps = 8;
 
 struct WalkWarpSmem {
     int stack[kStack];
     int leaves[kBatch];
+    EngineArgs e;
 };
 
-// One warp per tile: count (EMIT = false) or list (EMIT = true) its candidate leaves.
-template <int KER, int BW, bool CLIP, bool EMIT>
-__global__ void __launch_bounds__(kWalkWarps * 32) k_grid_walk(GridArgs a, int ntiles,
-                                                               uint32_t *cnt, const uint32_t *off,
-                                                               int *list) {
+// One warp per (ROI, tile): count (EMIT = false) or list (EMIT = true) its candidate leaves.
+template <int KER, int BW, bool CLIP, bool EMIT, int TZ>
+__global__ void __launch_bounds__(kWalkWarps * 32) k_mr_walk(MrArgs a, uint32_t *cnt,
+                                                             const uint32_t *off, int *list) {
     __shared__ WalkWarpSmem W[kWalkWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x * kWalkWarps + warp;
-    if (tile >= ntiles) return;
+    const int gt = blockIdx.x * kWalkWarps + warp;
+    if (gt >= a.ntiles) return;
     WalkWarpSmem &S = W[warp];
+    const RoiDesc &r = a.rois[a.tile_roi[gt]];
+    if (lane == 0) set_roi_engine(S.e, a.e, r);
+    __syncwarp();
     int gx0, gy0, gz0, nv[3];
-    tile_origin(a, tile, gx0, gy0, gz0, nv);
+    tile_origin<TZ>(r, gt - r.tile_base, gx0, gy0, gz0, nv);
     float tlo[3], thi[3];
-    tlo[0] = a.axis[gx0].x;
-    thi[0] = a.axis[gx0 + nv[0] - 1].x;
-    tlo[1] = a.axis[a.nx + gy0].x;
-    thi[1] = a.axis[a.nx + gy0 + nv[1] - 1].x;
-    tlo[2] = a.axis[a.nx + a.ny + gz0].x;
-    thi[2] = a.axis[a.nx + a.ny + gz0 + nv[2] - 1].x;
-    float uni[3];
-    {
-        const DensityParams *dp = a.e.dp;
-        uni[0] = dp->ell_uniform[0];
-        uni[1] = dp->ell_uniform[1];
-        uni[2] = dp->ell_uniform[2];
-    }
-    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, uni, node, tlo, thi); };
+    tlo[0] = r.axis[gx0].x;
+    thi[0] = r.axis[gx0 + nv[0] - 1].x;
+    tlo[1] = r.axis[r.nx + gy0].x;
+    thi[1] = r.axis[r.nx + gy0 + nv[1] - 1].x;
+    tlo[2] = r.axis[r.nx + r.ny + gz0].x;
+    thi[2] = r.axis[r.nx + r.ny + gz0 + nv[2] - 1].x;
+    float uni[3] = {r.dp->ell_uniform[0], r.dp->ell_uniform[1], r.dp->ell_uniform[2]};
+    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(S.e, uni, node, tlo, thi); };
     int spv;
-    int nl = warp_walk_start(a.e.tv, test, S.stack, spv, S.leaves);
+    int nl = warp_walk_start(S.e.tv, test, S.stack, spv, S.leaves);
     uint32_t total = 0;
-    const uint32_t base = EMIT ? off[tile] : 0u;
+    const uint32_t base = EMIT ? off[gt] : 0u;
     while (true) {
         if (nl == 0) {
             if (spv == 0) break;
-            nl = warp_walk(a.e.tv, test, S.stack, spv, S.leaves, kBatch);
+            nl = warp_walk(S.e.tv, test, S.stack, spv, S.leaves, kBatch);
             if (nl == 0) break;
         }
         if (EMIT)
@@ -591,7 +635,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_grid_walk(GridArgs a, int n
         __syncwarp();
         nl = 0;
     }
-    if (!EMIT && lane == 0) cnt[tile] = total;
+    if (!EMIT && lane == 0) cnt[gt] = total;
 }
 
 __global__ void k_grid_item_counts(const uint32_t *__restrict__ cnt, int ntiles, uint32_t lpw,
@@ -610,65 +654,77 @@ __global__ void k_grid_items(const uint32_t *__restrict__ cnt, const uint32_t *_
         items[ioff[t] + i] = make_int4(t, (int)(b + i * lpw), (int)(b + min(n, (i + 1) * lpw)), 0);
 }
 
-template <int KER, int BW, bool CLIP, bool CNT>
+template <int KER, int BW, bool CLIP, bool CNT, int TZ>
 __global__ void __launch_bounds__(kGridThreads, 3)
-    k_grid_work(GridArgs a, const int4 *__restrict__ items, const uint32_t *__restrict__ n_items,
-                const int *__restrict__ list, double *__restrict__ part, unsigned int *next) {
+    k_mr_work(MrArgs a, const int4 *__restrict__ items, const uint32_t *__restrict__ n_items,
+              const int *__restrict__ list, double *__restrict__ part, unsigned int *next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GridSmem &S = *reinterpret_cast<GridSmem *>(smem_raw);
+    GridSmemT<TZ> &S = *reinterpret_cast<GridSmemT<TZ> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
     const uint32_t nitems = *n_items;
     unsigned long long npairs = 0;
+    int cur_roi = -1;
     while (true) {
         if (tid == 0) S.item = (int)atomicAdd(next, 1u);
         __syncthreads();
         const int item = S.item;
         if ((uint32_t)item >= nitems) break;
         const int4 it = items[item];
-        const TileGeom g = tile_setup(a, S, it.x);
-        float acc[kTileZ], sum[kTileZ], cmp[kTileZ];
+        const int ri = a.tile_roi[it.x];
+        if (ri != cur_roi) {  // uniform across the block
+            if (tid == 0) {
+                S.roi = a.rois[ri];
+                set_roi_engine(S.e, a.e, S.roi);
+            }
+            cur_roi = ri;
+            __syncthreads();
+        }
+        const TileGeom g = tile_setup<TZ>(S, it.x - S.roi.tile_base);
+        float acc[TZ], sum[TZ], cmp[TZ];
 #pragma unroll
-        for (int k = 0; k < kTileZ; ++k) acc[k] = sum[k] = cmp[k] = 0.f;
+        for (int k = 0; k < TZ; ++k) acc[k] = sum[k] = cmp[k] = 0.f;
         unsigned long long np = 0;
         for (int lb = it.y; lb < it.z; lb += kStage / kLeaf) {
-            grid_chunk<KER, BW, CLIP, CNT>(a, S, g, list + lb, min(kStage / kLeaf, it.z - lb), acc, np);
-            fold(acc, sum, cmp);
+            grid_chunk<KER, BW, CLIP, CNT, TZ>(S, g, list + lb, min(kStage / kLeaf, it.z - lb), acc, np);
+            fold<TZ>(acc, sum, cmp);
         }
         if (CNT && cx < g.nv[0] && cy < g.nv[1]) npairs += np;
-        double *o = part + ((int64_t)item * kGridThreads + tid) * kTileZ;
+        double *o = part + ((int64_t)item * kGridThreads + tid) * TZ;
 #pragma unroll
-        for (int k = 0; k < kTileZ; ++k) o[k] = (double)sum[k] + (double)cmp[k];
+        for (int k = 0; k < TZ; ++k) o[k] = (double)sum[k] + (double)cmp[k];
     }
-    if (CNT) count_pairs_out(a, npairs);
+    if (CNT) count_pairs_out(a.pairs, npairs);
 }
 
-// Per tile: sum the items' partial grids in item order, scale, write, and the tile's mass.
-__global__ void __launch_bounds__(kGridThreads) k_grid_reduce(GridArgs a,
-                                                              const uint32_t *__restrict__ ic,
-                                                              const uint32_t *__restrict__ ioff,
-                                                              const double *__restrict__ part) {
+// Per (ROI, tile): sum the items' partial grids in item order, scale, write, and the tile's mass.
+template <int TZ>
+__global__ void __launch_bounds__(kGridThreads) k_mr_reduce(MrArgs a, const uint32_t *__restrict__ ic,
+                                                            const uint32_t *__restrict__ ioff,
+                                                            const double *__restrict__ part) {
     __shared__ double red[kGridThreads / 32];
-    const int tile = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gt = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
+    const RoiDesc &r = a.rois[a.tile_roi[gt]];
+    const int tile = gt - r.tile_base;
     int gx0, gy0, gz0, nv[3];
-    tile_origin(a, tile, gx0, gy0, gz0, nv);
-    const double inv_neff = a.e.dp->inv_neff;
-    double v[kTileZ];
+    tile_origin<TZ>(r, tile, gx0, gy0, gz0, nv);
+    const double inv_neff = r.dp->inv_neff;
+    double v[TZ];
 #pragma unroll
-    for (int k = 0; k < kTileZ; ++k) v[k] = 0.0;
-    const uint32_t i0 = ioff[tile], ni = ic[tile];
+    for (int k = 0; k < TZ; ++k) v[k] = 0.0;
+    const uint32_t i0 = ioff[gt], ni = ic[gt];
     for (uint32_t i = 0; i < ni; ++i) {
-        const double *pp = part + ((int64_t)(i0 + i) * kGridThreads + tid) * kTileZ;
+        const double *pp = part + ((int64_t)(i0 + i) * kGridThreads + tid) * TZ;
 #pragma unroll
-        for (int k = 0; k < kTileZ; ++k) v[k] += pp[k];
+        for (int k = 0; k < TZ; ++k) v[k] += pp[k];
     }
     double msum = 0.0;
     if (cx < nv[0] && cy < nv[1]) {
-        float *o = a.out + ((int64_t)gz0 * a.ny + (gy0 + cy)) * a.nx + (gx0 + cx);
-        const int64_t zs = (int64_t)a.nx * a.ny;
+        float *o = r.out + ((int64_t)gz0 * r.ny + (gy0 + cy)) * r.nx + (gx0 + cx);
+        const int64_t zs = (int64_t)r.nx * r.ny;
 #pragma unroll
-        for (int k = 0; k < kTileZ; ++k) {
+        for (int k = 0; k < TZ; ++k) {
             if (k < nv[2]) {
                 const float fv = (float)(v[k] * inv_neff);
                 o[k * zs] = fv;
@@ -683,7 +739,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_reduce(GridArgs a,
     if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < kGridThreads / 32; ++w) t += red[w];
-        a.mass_part[tile] = t;
+        r.mass_part[tile] = t;
     }
 }
 
@@ -703,9 +759,31 @@ __global__ void k_mass_final(const double *__restrict__ part, int64_t n, double 
     }
 }
 
+// One block per ROI: its tiles' masses in order, times its cell volume.
+__global__ void k_mr_mass(const RoiDesc *__restrict__ rois, const double *__restrict__ cells,
+                          int nroi, double *__restrict__ mass) {
+    __shared__ double red[32];
+    const int ri = blockIdx.x;
+    if (ri >= nroi) return;
+    const RoiDesc &r = rois[ri];
+    const int nt = r.tiles_x * r.tiles_y * r.tiles_z;
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) t += r.mass_part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        mass[ri] = s * cells[ri];
+    }
+}
+
+// ---- monolithic dispatch (allocation-free path) ----------------------------
 template <int KER, int BW, bool CLIP, bool CNT>
 static cudaError_t launch_grid_t(const GridArgs &a, unsigned tiles, cudaStream_t s) {
-    const size_t smem = sizeof(GridSmem);
+    const size_t smem = sizeof(GridSmemT<kTileZ>);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_grid<KER, BW, CLIP, CNT>,
@@ -736,83 +814,134 @@ static cudaError_t dispatch_grid(int bw, bool clip, const GridArgs &a, unsigned 
     }
 }
 
-// The split pipeline for one (kernel, bandwidth mode, clip) combination.
-template <int KER, int BW, bool CLIP>
-static sf_status split_grid(const GridArgs &a0, int ntiles, cudaStream_t s) {
-    GridArgs a = a0;
-    Scratch sc(s);
-    uint32_t *cnt = sc.get<uint32_t>(ntiles);
-    uint32_t *off = sc.get<uint32_t>(ntiles);
-    uint32_t *tot = sc.get<uint32_t>(2);
-    SF_TRY_SCRATCH(sc);
-    const unsigned wb = blocks_for(ntiles, kWalkWarps);
-    SF_TRY_CUDA(launch(k_grid_walk<KER, BW, CLIP, false>, dim3(wb), dim3(kWalkWarps * 32), 0, s, a,
-                       ntiles, cnt, (const uint32_t *)nullptr, (int *)nullptr));
-    SF_TRY(scan_u32(cnt, off, ntiles, tot, s));
-    uint32_t total = 0;
-    SF_TRY_CUDA(cudaMemcpyAsync(&total, tot, sizeof total, cudaMemcpyDeviceToHost, s));
+// ---- split pipeline ---------------------------------------------------------
+// Sizing: count candidate leaves of every (ROI, tile); returns the total (syncs).
+template <int KER, int BW, bool CLIP, int TZ>
+static sf_status mr_count(const MrArgs &a, uint32_t *cnt, uint32_t *off, uint32_t *tot,
+                          uint32_t *h_total, cudaStream_t s) {
+    const unsigned wb = blocks_for(a.ntiles, kWalkWarps);
+    SF_TRY_CUDA(launch(k_mr_walk<KER, BW, CLIP, false, TZ>, dim3(wb), dim3(kWalkWarps * 32), 0, s, a,
+                       cnt, (const uint32_t *)nullptr, (int *)nullptr));
+    SF_TRY(scan_u32(cnt, off, a.ntiles, tot, s));
+    SF_TRY_CUDA(cudaMemcpyAsync(h_total, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     SF_TRY_CUDA(cudaStreamSynchronize(s));
-    int dev = 0, sms = 0, per_sm = 0;
-    SF_TRY_CUDA(cudaGetDevice(&dev));
-    SF_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t smem = sizeof(GridSmem);
-    static bool attr = false;
-    if (!attr) {
-        SF_TRY_CUDA(cudaFuncSetAttribute(k_grid_work<KER, BW, CLIP, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        SF_TRY_CUDA(cudaFuncSetAttribute(k_grid_work<KER, BW, CLIP, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
-    SF_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_work<KER, BW, CLIP, false>,
-                                                              kGridThreads, smem));
-    if (per_sm < 1) per_sm = 1;
-    const int64_t slots = (int64_t)sms * per_sm;
-    // leaves per item: about four items per resident CTA, a multiple of the chunk
-    uint32_t lpw = (uint32_t)std::max<int64_t>(16, (total + 4 * slots - 1) / (4 * slots));
-    lpw = (lpw + 3) & ~3u;
-    const int64_t max_items = ntiles + total / lpw + 1;
-    int *list = sc.get<int>(std::max<int64_t>(1, total));
-    uint32_t *ic = sc.get<uint32_t>(ntiles);
-    uint32_t *ioff = sc.get<uint32_t>(ntiles);
-    int4 *items = sc.get<int4>(max_items);
-    double *part = sc.get<double>(max_items * kGridThreads * kTileZ);
-    unsigned int *next = sc.get<unsigned int>(1);
-    SF_TRY_SCRATCH(sc);
-    SF_TRY_CUDA(launch(k_grid_walk<KER, BW, CLIP, true>, dim3(wb), dim3(kWalkWarps * 32), 0, s, a,
-                       ntiles, (uint32_t *)nullptr, (const uint32_t *)off, list));
-    SF_TRY_CUDA(launch(k_grid_item_counts, dim3(blocks_for(ntiles, 256)), dim3(256), 0, s,
-                       (const uint32_t *)cnt, ntiles, lpw, ic));
-    SF_TRY(scan_u32(ic, ioff, ntiles, tot + 1, s));
-    SF_TRY_CUDA(launch(k_grid_items, dim3(blocks_for(ntiles, 256)), dim3(256), 0, s,
-                       (const uint32_t *)cnt, (const uint32_t *)off, (const uint32_t *)ic,
-                       (const uint32_t *)ioff, ntiles, lpw, items));
-    SF_TRY_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned int), s));
-    {
-        KTimer t(a.pairs ? "k_grid_work_count" : "k_grid_work", s);
-        if (a.pairs)
-            SF_TRY_CUDA(launch(k_grid_work<KER, BW, CLIP, true>, dim3((unsigned)slots), dim3(kGridThreads),
-                               smem, s, a, (const int4 *)items, (const uint32_t *)(tot + 1),
-                               (const int *)list, part, next));
-        else
-            SF_TRY_CUDA(launch(k_grid_work<KER, BW, CLIP, false>, dim3((unsigned)slots), dim3(kGridThreads),
-                               smem, s, a, (const int4 *)items, (const uint32_t *)(tot + 1),
-                               (const int *)list, part, next));
-    }
-    SF_TRY_CUDA(launch(k_grid_reduce, dim3(ntiles), dim3(kGridThreads), 0, s, a, (const uint32_t *)ic,
-                       (const uint32_t *)ioff, (const double *)part));
     return SF_OK;
 }
 
-template <int KER>
-static sf_status dispatch_split(int bw, bool clip, const GridArgs &a, int ntiles, cudaStream_t s) {
+template <int KER, int BW, bool CLIP, bool CNT, int TZ>
+static sf_status mr_work_attr(int *per_sm) {
+    const size_t smem = sizeof(GridSmemT<TZ>);
+    static bool attr = false;
+    if (!attr) {
+        SF_TRY_CUDA(cudaFuncSetAttribute(k_mr_work<KER, BW, CLIP, CNT, TZ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    SF_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_mr_work<KER, BW, CLIP, CNT, TZ>,
+                                                              kGridThreads, smem));
+    if (*per_sm < 1) *per_sm = 1;
+    return SF_OK;
+}
+
+// Buffers of the execution phase, sized from the count.
+struct MrBuffers {
+    uint32_t *cnt, *off, *tot, *ic, *ioff;
+    int *list;
+    int4 *items;
+    double *part;
+    unsigned int *next;
+    uint32_t lpw;
+    int64_t slots;
+};
+
+// Execution: list, items, persistent work, ordered reduce (no host sync; capturable).
+template <int KER, int BW, bool CLIP, bool CNT, int TZ>
+static sf_status mr_exec(const MrArgs &a, const MrBuffers &b, cudaStream_t s) {
+    const unsigned wb = blocks_for(a.ntiles, kWalkWarps);
+    SF_TRY_CUDA(launch(k_mr_walk<KER, BW, CLIP, true, TZ>, dim3(wb), dim3(kWalkWarps * 32), 0, s, a,
+                       (uint32_t *)nullptr, (const uint32_t *)b.off, b.list));
+    SF_TRY_CUDA(launch(k_grid_item_counts, dim3(blocks_for(a.ntiles, 256)), dim3(256), 0, s,
+                       (const uint32_t *)b.cnt, a.ntiles, b.lpw, b.ic));
+    SF_TRY(scan_u32(b.ic, b.ioff, a.ntiles, b.tot + 1, s));
+    SF_TRY_CUDA(launch(k_grid_items, dim3(blocks_for(a.ntiles, 256)), dim3(256), 0, s,
+                       (const uint32_t *)b.cnt, (const uint32_t *)b.off, (const uint32_t *)b.ic,
+                       (const uint32_t *)b.ioff, a.ntiles, b.lpw, b.items));
+    SF_TRY_CUDA(cudaMemsetAsync(b.next, 0, sizeof(unsigned int), s));
+    {
+        KTimer t(CNT ? "k_grid_work_count" : "k_grid_work", s);
+        SF_TRY_CUDA(launch(k_mr_work<KER, BW, CLIP, CNT, TZ>, dim3((unsigned)b.slots), dim3(kGridThreads),
+                           sizeof(GridSmemT<TZ>), s, a, (const int4 *)b.items,
+                           (const uint32_t *)(b.tot + 1), (const int *)b.list, b.part, b.next));
+    }
+    SF_TRY_CUDA(launch(k_mr_reduce<TZ>, dim3(a.ntiles), dim3(kGridThreads), 0, s, a,
+                       (const uint32_t *)b.ic, (const uint32_t *)b.ioff, (const double *)b.part));
+    return SF_OK;
+}
+
+// Plan the buffers of an execution from the candidate total.
+template <int KER, int BW, bool CLIP, bool CNT, int TZ>
+static sf_status mr_plan(const MrArgs &a, uint32_t total, int items_per_slot, MrBuffers &b,
+                         Scratch *sc, std::vector<void *> *owned, cudaStream_t s) {
+    int dev = 0, sms = 0, per_sm = 0;
+    SF_TRY_CUDA(cudaGetDevice(&dev));
+    SF_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SF_TRY((mr_work_attr<KER, BW, CLIP, CNT, TZ>(&per_sm)));
+    b.slots = (int64_t)sms * per_sm;
+    const int64_t ips = std::max(1, items_per_slot);
+    uint32_t lpw = (uint32_t)std::max<int64_t>(16, (total + ips * b.slots - 1) / (ips * b.slots));
+    b.lpw = (lpw + 3) & ~3u;
+    const int64_t max_items = a.ntiles + total / b.lpw + 1;
+    auto get = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (sc) {
+            p = sc->get<unsigned char>((int64_t)bytes);
+        } else if (cudaMalloc(&p, bytes) == cudaSuccess) {
+            owned->push_back(p);
+        } else {
+            p = nullptr;
+        }
+        return p;
+    };
+    b.list = (int *)get(sizeof(int) * std::max<int64_t>(1, total));
+    b.ic = (uint32_t *)get(sizeof(uint32_t) * a.ntiles);
+    b.ioff = (uint32_t *)get(sizeof(uint32_t) * a.ntiles);
+    b.items = (int4 *)get(sizeof(int4) * max_items);
+    b.part = (double *)get(sizeof(double) * max_items * kGridThreads * TZ);
+    b.next = (unsigned int *)get(sizeof(unsigned int));
+    if (!b.list || !b.ic || !b.ioff || !b.items || !b.part || !b.next)
+        return fail(SF_ERR_OOM, "grid work buffers (%lld items)", (long long)max_items);
+    return SF_OK;
+}
+
+template <int KER, int BW, bool CLIP, int TZ>
+static sf_status mr_once(const MrArgs &a, int items_per_slot, cudaStream_t s) {
+    Scratch sc(s);
+    MrBuffers b;
+    b.cnt = sc.get<uint32_t>(a.ntiles);
+    b.off = sc.get<uint32_t>(a.ntiles);
+    b.tot = sc.get<uint32_t>(2);
+    SF_TRY_SCRATCH(sc);
+    uint32_t total = 0;
+    SF_TRY((mr_count<KER, BW, CLIP, TZ>(a, b.cnt, b.off, b.tot, &total, s)));
+    if (a.pairs) {
+        SF_TRY((mr_plan<KER, BW, CLIP, true, TZ>(a, total, items_per_slot, b, &sc, nullptr, s)));
+        SF_TRY_SCRATCH(sc);
+        return mr_exec<KER, BW, CLIP, true, TZ>(a, b, s);
+    }
+    SF_TRY((mr_plan<KER, BW, CLIP, false, TZ>(a, total, items_per_slot, b, &sc, nullptr, s)));
+    SF_TRY_SCRATCH(sc);
+    return mr_exec<KER, BW, CLIP, false, TZ>(a, b, s);
+}
+
+template <int KER, int TZ>
+static sf_status dispatch_once(int bw, bool clip, const MrArgs &a, int ips, cudaStream_t s) {
     switch (bw * 2 + (clip ? 1 : 0)) {
-        case BW_ISO * 2 + 0: return split_grid<KER, BW_ISO, false>(a, ntiles, s);
-        case BW_ISO * 2 + 1: return split_grid<KER, BW_ISO, true>(a, ntiles, s);
-        case BW_UNIFORM * 2 + 0: return split_grid<KER, BW_UNIFORM, false>(a, ntiles, s);
-        case BW_UNIFORM * 2 + 1: return split_grid<KER, BW_UNIFORM, true>(a, ntiles, s);
-        case BW_ANISO * 2 + 0: return split_grid<KER, BW_ANISO, false>(a, ntiles, s);
-        default: return split_grid<KER, BW_ANISO, true>(a, ntiles, s);
+        case BW_ISO * 2 + 0: return mr_once<KER, BW_ISO, false, TZ>(a, ips, s);
+        case BW_ISO * 2 + 1: return mr_once<KER, BW_ISO, true, TZ>(a, ips, s);
+        case BW_UNIFORM * 2 + 0: return mr_once<KER, BW_UNIFORM, false, TZ>(a, ips, s);
+        case BW_UNIFORM * 2 + 1: return mr_once<KER, BW_UNIFORM, true, TZ>(a, ips, s);
+        case BW_ANISO * 2 + 0: return mr_once<KER, BW_ANISO, false, TZ>(a, ips, s);
+        default: return mr_once<KER, BW_ANISO, true, TZ>(a, ips, s);
     }
 }
 
@@ -834,11 +963,8 @@ static EngineArgs engine_args(sf_index *idx, const sf_box &roi, const DensityCal
     return e;
 }
 
-sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
-                       const DensityCall &call, float *d_out, double *d_mass, cudaStream_t s,
-                       unsigned long long *d_pairs) {
-    // node coordinates r_k(i) = lo_k + i s_k in double, split into float (hi, lo)
-    std::vector<float2> ax((size_t)g.nx + g.ny + g.nz);
+// Node coordinates r_k(i) = lo_k + i s_k in double, split into float (hi, lo).
+static void node_axes(const GridSpec &g, float2 *ax) {
     const int nd[3] = {g.nx, g.ny, g.nz};
     size_t o = 0;
     for (int k = 0; k < 3; ++k)
@@ -847,32 +973,58 @@ sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
             const float h = (float)r;
             ax[o++] = make_float2(h, (float)(r - (double)h));
         }
-    GridArgs a;
-    a.e = engine_args(idx, roi, call);
-    a.nx = g.nx;
-    a.ny = g.ny;
-    a.nz = g.nz;
-    a.tiles_x = (g.nx + kTileX - 1) / kTileX;
-    a.tiles_y = (g.ny + kTileY - 1) / kTileY;
-    a.tiles_z = (g.nz + kTileZ - 1) / kTileZ;
-    const int64_t tiles = (int64_t)a.tiles_x * a.tiles_y * a.tiles_z;
-    if (tiles >= (int64_t(1) << 31)) return fail(SF_ERR_INVALID_ARG, "grid too large");
+}
+
+static RoiDesc roi_desc(const GridSpec &g, int tz, const float2 *axis, int tile_base, float *out,
+                        double *mass_part, const DensityParams *dp, const sf_box &roi) {
+    RoiDesc r;
+    r.axis = axis;
+    r.nx = g.nx;
+    r.ny = g.ny;
+    r.nz = g.nz;
+    r.tiles_x = (g.nx + kTileX - 1) / kTileX;
+    r.tiles_y = (g.ny + kTileY - 1) / kTileY;
+    r.tiles_z = (g.nz + tz - 1) / tz;
+    r.tile_base = tile_base;
+    r.out = out;
+    r.mass_part = mass_part;
+    r.dp = dp;
+    float_bounds(roi.lo, roi.hi, r.blo, r.bhi);
+    return r;
+}
+
+sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
+                       const DensityCall &call, float *d_out, double *d_mass, cudaStream_t s,
+                       unsigned long long *d_pairs) {
+    constexpr int TZ = kTileZ;
+    std::vector<float2> ax((size_t)g.nx + g.ny + g.nz);
+    node_axes(g, ax.data());
+    const int64_t tiles = (int64_t)((g.nx + kTileX - 1) / kTileX) * ((g.ny + kTileY - 1) / kTileY) *
+                          ((g.nz + TZ - 1) / TZ);
+    if (tiles >= (int64_t(1) << 30)) return fail(SF_ERR_INVALID_ARG, "grid too large");
     Scratch sc(s);
     float2 *d_axis = sc.get<float2>((int64_t)ax.size());
     double *mass_part = sc.get<double>(tiles);
+    RoiDesc *d_roi = sc.get<RoiDesc>(1);
+    int *tile_roi = sc.get<int>(tiles);
     SF_TRY_SCRATCH(sc);
     SF_TRY_CUDA(cudaMemcpyAsync(d_axis, ax.data(), ax.size() * sizeof(float2),
                                 cudaMemcpyHostToDevice, s));
-    a.axis = d_axis;
-    a.out = d_out;
-    a.mass_part = mass_part;
+    const RoiDesc r = roi_desc(g, TZ, d_axis, 0, d_out, mass_part, call.dp, roi);
+    SF_TRY_CUDA(cudaMemcpyAsync(d_roi, &r, sizeof r, cudaMemcpyHostToDevice, s));
+    SF_TRY_CUDA(cudaMemsetAsync(tile_roi, 0, sizeof(int) * tiles, s));
+    MrArgs a;
+    a.e = engine_args(idx, roi, call);
+    a.rois = d_roi;
+    a.tile_roi = tile_roi;
+    a.ntiles = (int)tiles;
     a.pairs = d_pairs;
     {
         KTimer t(d_pairs ? "k_grid_count" : "k_grid", s);
         if (call.kernel == SF_K_EPAN)
-            SF_TRY(dispatch_split<SF_K_EPAN>(call.bw, call.clip != 0, a, (int)tiles, s));
+            SF_TRY((dispatch_once<SF_K_EPAN, TZ>(call.bw, call.clip != 0, a, 4, s)));
         else
-            SF_TRY(dispatch_split<SF_K_GAUSS3>(call.bw, call.clip != 0, a, (int)tiles, s));
+            SF_TRY((dispatch_once<SF_K_GAUSS3, TZ>(call.bw, call.clip != 0, a, 4, s)));
     }
     if (d_mass) {
         const double cell = g.s[0] * g.s[1] * g.s[2];
@@ -890,17 +1042,9 @@ sf_status density_grid_prealloc(sf_index *idx, const sf_box &roi, const GridSpec
                                 double *d_mass_part, float *d_out, double *d_mass, cudaStream_t s) {
     GridArgs a;
     a.e = engine_args(idx, roi, call);
-    a.nx = g.nx;
-    a.ny = g.ny;
-    a.nz = g.nz;
-    a.tiles_x = (g.nx + kTileX - 1) / kTileX;
-    a.tiles_y = (g.ny + kTileY - 1) / kTileY;
-    a.tiles_z = (g.nz + kTileZ - 1) / kTileZ;
-    const int64_t tiles = (int64_t)a.tiles_x * a.tiles_y * a.tiles_z;
-    a.axis = d_axis;
-    a.out = d_out;
-    a.mass_part = d_mass_part;
+    a.roi = roi_desc(g, kTileZ, d_axis, 0, d_out, d_mass_part, call.dp, roi);
     a.pairs = nullptr;
+    const int64_t tiles = (int64_t)a.roi.tiles_x * a.roi.tiles_y * a.roi.tiles_z;
     cudaError_t e = (call.kernel == SF_K_EPAN)
                         ? dispatch_grid<SF_K_EPAN>(call.bw, call.clip != 0, a, (unsigned)tiles, s)
                         : dispatch_grid<SF_K_GAUSS3>(call.bw, call.clip != 0, a, (unsigned)tiles, s);
@@ -916,6 +1060,198 @@ sf_status density_grid_prealloc(sf_index *idx, const sf_box &roi, const GridSpec
 int64_t grid_tile_count(const GridSpec &g) {
     return (int64_t)((g.nx + kTileX - 1) / kTileX) * ((g.ny + kTileY - 1) / kTileY) *
            ((g.nz + kTileZ - 1) / kTileZ);
+}
+
+// ===========================================================================
+// Batched grids: many ROIs in one persistent execution, replayed from a graph
+// ===========================================================================
+struct BatchPlan {
+    sf_index *idx = nullptr;
+    int nroi = 0;
+    int kernel = 0, bw = 0;
+    bool clip = false;
+    int tz = 8, ips = 4;
+    bool use_graph = true;
+    std::vector<RoiDesc> h_rois;       // host copy (out pointers updated per run)
+    std::vector<void *> owned;         // cudaMalloc'ed buffers
+    RoiDesc *d_rois = nullptr;
+    double *d_mass = nullptr;
+    MrArgs a;
+    MrBuffers b;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+template <int KER, int BW, bool CLIP, int TZ>
+static sf_status batch_build(BatchPlan &P, cudaStream_t s) {
+    uint32_t total = 0;
+    SF_TRY((mr_count<KER, BW, CLIP, TZ>(P.a, P.b.cnt, P.b.off, P.b.tot, &total, s)));
+    SF_TRY((mr_plan<KER, BW, CLIP, false, TZ>(P.a, total, P.ips, P.b, nullptr, &P.owned, s)));
+    if (!P.use_graph) return SF_OK;
+    // capture the execution once, on a private stream (the caller's may be the
+    // legacy default stream, which cannot be captured); runs replay it on theirs
+    cudaStream_t cs = nullptr;
+    SF_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return fail(SF_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(ce));
+    }
+    sf_status st = mr_exec<KER, BW, CLIP, false, TZ>(P.a, P.b, cs);
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (st != SF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    SF_TRY_CUDA(ce);
+    P.graph = g;
+    SF_TRY_CUDA(cudaGraphInstantiate(&P.exec, g, 0));
+    return SF_OK;
+}
+
+template <int KER, int BW, bool CLIP, int TZ>
+static sf_status batch_exec(BatchPlan &P, cudaStream_t s) {
+    if (P.exec) {
+        KTimer t("k_batch_graph", s);
+        SF_TRY_CUDA(cudaGraphLaunch(P.exec, s));
+        g_launches.fetch_add(8, std::memory_order_relaxed);  // kernels inside the graph
+        return SF_OK;
+    }
+    return mr_exec<KER, BW, CLIP, false, TZ>(P.a, P.b, s);
+}
+
+template <int KER, int TZ>
+static sf_status batch_dispatch(BatchPlan &P, bool build, cudaStream_t s) {
+    switch (P.bw * 2 + (P.clip ? 1 : 0)) {
+        case BW_ISO * 2 + 0: return build ? batch_build<KER, BW_ISO, false, TZ>(P, s) : batch_exec<KER, BW_ISO, false, TZ>(P, s);
+        case BW_ISO * 2 + 1: return build ? batch_build<KER, BW_ISO, true, TZ>(P, s) : batch_exec<KER, BW_ISO, true, TZ>(P, s);
+        case BW_UNIFORM * 2 + 0: return build ? batch_build<KER, BW_UNIFORM, false, TZ>(P, s) : batch_exec<KER, BW_UNIFORM, false, TZ>(P, s);
+        default: return build ? batch_build<KER, BW_UNIFORM, true, TZ>(P, s) : batch_exec<KER, BW_UNIFORM, true, TZ>(P, s);
+    }
+}
+
+static sf_status batch_call(BatchPlan &P, bool build, cudaStream_t s) {
+    if (P.kernel == SF_K_EPAN)
+        return P.tz == 4 ? batch_dispatch<SF_K_EPAN, 4>(P, build, s) : batch_dispatch<SF_K_EPAN, 8>(P, build, s);
+    return P.tz == 4 ? batch_dispatch<SF_K_GAUSS3, 4>(P, build, s) : batch_dispatch<SF_K_GAUSS3, 8>(P, build, s);
+}
+
+void batch_free(BatchPlan *P) {
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    for (void *p : P->owned) cudaFree(p);
+    delete P;
+}
+
+// rois/grids: nroi boxes and GridSpecs; dps: device DensityParams per ROI (owned by the plan)
+sf_status batch_create(sf_index *idx, int nroi, const sf_box *rois, const GridSpec *grids,
+                       int kernel, int bw, bool clip, DensityParams *d_dps, int tz, int ips,
+                       bool use_graph, cudaStream_t s, BatchPlan **out) {
+    BatchPlan *P = new BatchPlan();
+    P->idx = idx;
+    P->nroi = nroi;
+    P->kernel = kernel;
+    P->bw = bw;
+    P->clip = clip;
+    P->tz = (tz == 4) ? 4 : 8;
+    P->ips = ips;
+    P->use_graph = use_graph;
+    auto bail = [&](sf_status st) {
+        batch_free(P);
+        return st;
+    };
+    P->owned.push_back(d_dps);
+    int64_t naxis = 0, ntiles = 0;
+    std::vector<int64_t> tb(nroi);
+    for (int r = 0; r < nroi; ++r) {
+        naxis += grids[r].nx + grids[r].ny + grids[r].nz;
+        tb[r] = ntiles;
+        ntiles += (int64_t)((grids[r].nx + kTileX - 1) / kTileX) * ((grids[r].ny + kTileY - 1) / kTileY) *
+                  ((grids[r].nz + P->tz - 1) / P->tz);
+    }
+    if (ntiles >= (int64_t(1) << 30)) return bail(fail(SF_ERR_INVALID_ARG, "batch too large"));
+    std::vector<float2> ax(naxis);
+    std::vector<int> tile_roi(ntiles);
+    void *p_axis = nullptr, *p_rois = nullptr, *p_tr = nullptr, *p_mp = nullptr, *p_mass = nullptr,
+         *p_cnt = nullptr, *p_off = nullptr, *p_tot = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&p_axis, sizeof(float2) * naxis)) != cudaSuccess ||
+        (e = cudaMalloc(&p_rois, sizeof(RoiDesc) * nroi)) != cudaSuccess ||
+        (e = cudaMalloc(&p_tr, sizeof(int) * ntiles)) != cudaSuccess ||
+        (e = cudaMalloc(&p_mp, sizeof(double) * ntiles)) != cudaSuccess ||
+        (e = cudaMalloc(&p_mass, sizeof(double) * 2 * nroi)) != cudaSuccess ||
+        (e = cudaMalloc(&p_cnt, sizeof(uint32_t) * ntiles)) != cudaSuccess ||
+        (e = cudaMalloc(&p_off, sizeof(uint32_t) * ntiles)) != cudaSuccess ||
+        (e = cudaMalloc(&p_tot, sizeof(uint32_t) * 2)) != cudaSuccess) {
+        for (void *q : {p_axis, p_rois, p_tr, p_mp, p_mass, p_cnt, p_off, p_tot})
+            if (q) cudaFree(q);
+        return bail(fail(SF_ERR_OOM, "batch plan: %s", cudaGetErrorString(e)));
+    }
+    for (void *q : {p_axis, p_rois, p_tr, p_mp, p_mass, p_cnt, p_off, p_tot}) P->owned.push_back(q);
+    float2 *d_axis = (float2 *)p_axis;
+    double *d_mp = (double *)p_mp;
+    P->d_rois = (RoiDesc *)p_rois;
+    P->d_mass = (double *)p_mass;
+    int64_t ao = 0;
+    P->h_rois.resize(nroi);
+    std::vector<double> cells(nroi);
+    for (int r = 0; r < nroi; ++r) {
+        node_axes(grids[r], ax.data() + ao);
+        P->h_rois[r] = roi_desc(grids[r], P->tz, d_axis + ao, (int)tb[r], nullptr, d_mp + tb[r],
+                                d_dps + r, rois[r]);
+        const int64_t nt = (r + 1 < nroi ? tb[r + 1] : ntiles) - tb[r];
+        for (int64_t t = 0; t < nt; ++t) tile_roi[tb[r] + t] = r;
+        ao += grids[r].nx + grids[r].ny + grids[r].nz;
+        cells[r] = grids[r].s[0] * grids[r].s[1] * grids[r].s[2];
+    }
+    if ((e = cudaMemcpyAsync(d_axis, ax.data(), sizeof(float2) * naxis, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->d_rois, P->h_rois.data(), sizeof(RoiDesc) * nroi, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p_tr, tile_roi.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P->d_mass + nroi, cells.data(), sizeof(double) * nroi, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return bail(fail(SF_ERR_CUDA, "batch plan upload: %s", cudaGetErrorString(e)));
+    sf_box any = rois[0];
+    DensityCall call;
+    call.kernel = kernel;
+    call.bw = bw;
+    call.clip = clip ? 1 : 0;
+    call.ell = nullptr;
+    call.dp = d_dps;
+    call.nell_override = nullptr;
+    P->a.e = engine_args(idx, any, call);
+    P->a.rois = P->d_rois;
+    P->a.tile_roi = (const int *)p_tr;
+    P->a.ntiles = (int)ntiles;
+    P->a.pairs = nullptr;
+    P->b.cnt = (uint32_t *)p_cnt;
+    P->b.off = (uint32_t *)p_off;
+    P->b.tot = (uint32_t *)p_tot;
+    sf_status st = batch_call(*P, true, s);
+    if (st != SF_OK) return bail(st);
+    *out = P;
+    return SF_OK;
+}
+
+sf_status batch_run(BatchPlan *P, float *const *outs, double *h_mass, cudaStream_t s) {
+    bool changed = false;
+    for (int r = 0; r < P->nroi; ++r)
+        if (P->h_rois[r].out != outs[r]) {
+            P->h_rois[r].out = outs[r];
+            changed = true;
+        }
+    if (changed)
+        SF_TRY_CUDA(cudaMemcpyAsync(P->d_rois, P->h_rois.data(), sizeof(RoiDesc) * P->nroi,
+                                    cudaMemcpyHostToDevice, s));
+    SF_TRY(batch_call(*P, false, s));
+    if (h_mass) {
+        SF_TRY_CUDA(launch(k_mr_mass, dim3(P->nroi), dim3(256), 0, s, (const RoiDesc *)P->d_rois,
+                           (const double *)(P->d_mass + P->nroi), P->nroi, P->d_mass));
+        SF_TRY_CUDA(cudaMemcpyAsync(h_mass, P->d_mass, sizeof(double) * P->nroi, cudaMemcpyDeviceToHost, s));
+        SF_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    return SF_OK;
 }
 
 // ===========================================================================

@@ -233,6 +233,14 @@ sf_status density_points(sf_index *idx, const sf_box &roi, const DensityCall &ca
 sf_status build_node_ell(sf_index *idx, int bw, const float4 *ell, const sf_box *clip_roi,
                          float4 *d_nell, cudaStream_t s);
 
+// Batched grids over many ROIs (sf_density.cu).
+struct BatchPlan;
+sf_status batch_create(sf_index *idx, int nroi, const sf_box *rois, const GridSpec *grids,
+                       int kernel, int bw, bool clip, DensityParams *d_dps, int tz, int ips,
+                       bool use_graph, cudaStream_t s, BatchPlan **out);
+sf_status batch_run(BatchPlan *P, float *const *outs, double *h_mass, cudaStream_t s);
+void batch_free(BatchPlan *P);
+
 // ---------------------------------------------------------------------------
 // kNN (sf_knn.cu)
 // ---------------------------------------------------------------------------

@@ -39,6 +39,8 @@ static std::vector<TimedPair> g_timed;
 
 KTimer::KTimer(const char *n, cudaStream_t st) : name(n), s(st) {
     if (!g_timing.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
         a = b = nullptr;
         return;

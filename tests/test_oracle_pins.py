@@ -293,3 +293,19 @@ def test_select_brute_force():
     assert int(np.sum(d <= t)) >= math.ceil(0.9 * 5000)
     assert int(np.sum(d < t)) < math.ceil(0.9 * 5000)
     assert sel.tolist() == [int(i) for i, v in zip(ids, d) if v > t]
+
+
+def test_ambiguous_mass_is_two_sided():
+    """A pair a hair outside the Gaussian cutoff (q = 9 (1 + 1e-7)) adds nothing to rho
+    but its untruncated kernel value to the ambiguous mass; one a hair inside adds to both."""
+    xyz = np.array([[0.8, 0.5, 0.5]], dtype=np.float32)
+    dx = float(np.float64(xyz[0, 0]) - 0.5)
+    node = np.array([[0.5, 0.5, 0.5]])
+    for side, inside in ((1 + 1e-7, False), (1 - 1e-7, True)):
+        h = dx / (3.0 * np.sqrt(side))
+        q = (dx / h) ** 2
+        assert (q < 9) == inside
+        out = oracle.density_at(xyz, np.array([[h, h, h]]), node, oracle.GAUSS3, 1.0)
+        val = np.exp(-0.5 * q) / ((2 * np.pi) ** 1.5 * h ** 3 * oracle.P3)
+        assert out["amb"][0] == pytest.approx(val, rel=1e-12)
+        assert out["rho"][0] == (pytest.approx(val, rel=1e-12) if inside else 0.0)
