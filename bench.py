@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="cloud size (smaller clouds are for profiling only, not bench lines)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop sample")
+    ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--no-count", action="store_true",
                     help="skip the pair-counting pass (value and roofline become null)")
     return ap.parse_args()
@@ -346,6 +348,11 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(args, L, torch, xyz, boxes, p, pairs_step, stream, world, barrier, dist)
 
+    # ---- serving loop: Poisson navigation stream over the resident index
+    serving = None
+    if not args.no_serve:
+        serving = run_serving(args, L, torch, d_xyz, p, rois)
+
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -368,6 +375,7 @@ def main():
                 "pairs_per_step": {"grid": pairs_grid, "points": pairs_pts},
                 "kernels_ms_per_step": {k: v["ms_total"] / args.steps for k, v in kern.items()},
                 "kernels_ms_per_roi": {k: v.get("per_roi_ms") for k, v in kern.items() if "per_roi_ms" in v},
+                "serving": serving,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -400,6 +408,38 @@ def load_traffic(kernel):
         return ent["dram_bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         return None
+
+
+def run_serving(args, L, torch, d_xyz, p, rois):
+    """Continuous admission of ROI recomputes (grid + point densities + selection)
+    arriving as a Poisson stream (mean 200/s) that walks zoom and pan over three
+    decades of scale with grid edges 64..256, on 4 slots (streams)."""
+    from paper_2601_20758_gb300 import serve
+    n = d_xyz.shape[0]
+    idx = L.sf_build_index(d_xyz)
+    try:
+        L.sf_bandwidths(idx, p)
+        centre = [(float(rois[-1][0][k]) + float(rois[-1][1][k])) / 2 for k in range(3)]
+        reqs = serve.navigation_requests(args.serve_requests, rate=200.0, centre=centre, seed=2601)
+        free, _ = torch.cuda.mem_get_info()
+        slots = 4
+        ex = serve.GpuExecutor(idx, p, L.SF_K_GAUSS3, n, slots=slots, max_nodes=256 ** 3)
+        srv = serve.Server(ex, slots=slots, mem_budget=int(0.5 * free), n_points=n)
+        try:
+            # warm the slots once (first-use costs), then replay the stream
+            warm = [serve.Request(-1 - i, r.lo, r.hi, r.dims) for i, r in enumerate(reqs[:slots])]
+            srv.replay(warm)
+            srv.completed.clear()
+            st = srv.replay(reqs)
+        finally:
+            srv.close()
+        st["rate_per_s"] = 200.0
+        st["stream"] = ("Poisson arrivals, zoom walk over log10 edge in [-3, 0] (sigma 0.1 decade), "
+                        "pan <= half an edge, grid edge in {64, 96, 128, 192, 256}^3, "
+                        "grid + point densities + 90th-percentile selection per request")
+        return st
+    finally:
+        L.sf_free_index(idx)
 
 
 def run_e2e(args, L, torch, xyz, boxes, p, pairs_step, stream, world, barrier, dist):

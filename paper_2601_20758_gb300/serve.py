@@ -1,0 +1,239 @@
+"""Serving loop for ROI density recomputes with continuous admission.
+
+Progressive navigation (the paper's Sec. 4.2: a new region of interest or a
+new scale triggers a density recompute) turns into a stream of recompute
+requests. The server keeps the index and the bandwidths resident on the GPU;
+requests wait in arrival order and are admitted as soon as a slot is free and
+their estimated device memory fits the budget; each slot runs its request
+(ROI grid -> ROI point densities -> threshold selection) on its own CUDA
+stream, so admitted requests overlap on the device. Latency = completion time
+- arrival time on the host clock.
+
+The executor is pluggable: ``GpuExecutor`` drives libscalefree through the C
+ABI; tests drive the admission logic with a fake executor on the CPU.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    lo: tuple
+    hi: tuple
+    dims: tuple
+    arrival: float = 0.0          # seconds on the server clock
+    select_pct: float = 90.0
+    want_points: bool = True
+    # filled by the server
+    admitted: float = math.nan
+    done: float = math.nan
+    status: str = "pending"
+    result: dict = field(default_factory=dict)
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def estimate_bytes(req: Request, n_points: int) -> int:
+    """Device memory a request holds while it runs: the grid output, the grid
+    work buffers (partial sums bounded by 16 B per node plus the candidate
+    lists), and the per-point scratch of the point densities (24 B per point)."""
+    g = int(req.dims[0]) * int(req.dims[1]) * int(req.dims[2])
+    pts = 24 * n_points if req.want_points else 0
+    return 4 * g + 16 * g + 8 * n_points // 32 + pts
+
+
+def percentile(values, q):
+    v = sorted(values)
+    if not v:
+        return None
+    k = max(1, math.ceil(q / 100.0 * len(v)))
+    return v[k - 1]
+
+
+class Server:
+    """Continuous admission over `slots` concurrent slots and a memory budget."""
+
+    def __init__(self, executor, slots: int = 4, mem_budget: int = 1 << 34, n_points: int = 0):
+        self.ex = executor
+        self.slots = slots
+        self.budget = mem_budget
+        self.n_points = n_points
+        self._lock = threading.Condition()
+        self._queue = collections.deque()
+        self._free_slots = list(range(slots))
+        self._in_flight = 0
+        self._running = 0
+        self._closed = False
+        self.max_concurrent = 0
+        self.max_bytes = 0
+        self.completed = []
+        self._t0 = time.perf_counter()
+        self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
+        self._dispatcher.start()
+
+    def now(self) -> float:
+        return time.perf_counter() - self._t0
+
+    def submit(self, req: Request):
+        need = estimate_bytes(req, self.n_points)
+        with self._lock:
+            if need > self.budget:
+                req.status = "rejected"      # can never fit, even alone
+                req.done = self.now()
+                self.completed.append(req)
+                return
+            req._need = need
+            self._queue.append(req)
+            self._lock.notify_all()
+
+    def _dispatch(self):
+        while True:
+            with self._lock:
+                while not self._closed and not (
+                        self._queue and self._free_slots
+                        and self._in_flight + self._queue[0]._need <= self.budget):
+                    self._lock.wait()
+                if self._closed and not self._queue:
+                    return
+                if not (self._queue and self._free_slots
+                        and self._in_flight + self._queue[0]._need <= self.budget):
+                    continue
+                req = self._queue.popleft()           # first come, first admitted
+                slot = self._free_slots.pop()
+                self._in_flight += req._need
+                self._running += 1
+                self.max_concurrent = max(self.max_concurrent, self._running)
+                self.max_bytes = max(self.max_bytes, self._in_flight)
+                req.admitted = self.now()
+                req.status = "running"
+            threading.Thread(target=self._work, args=(req, slot), daemon=True).start()
+
+    def _work(self, req: Request, slot: int):
+        try:
+            req.result = self.ex.run(req, slot)
+            req.status = "done"
+        except Exception as e:  # noqa: BLE001  (recorded per request)
+            req.status = f"error: {e}"
+        with self._lock:
+            req.done = self.now()
+            self._in_flight -= req._need
+            self._running -= 1
+            self._free_slots.append(slot)
+            self.completed.append(req)
+            self._lock.notify_all()
+
+    def drain(self, n_expected: int, timeout: float = 600.0):
+        deadline = time.perf_counter() + timeout
+        with self._lock:
+            while len(self.completed) < n_expected:
+                left = deadline - time.perf_counter()
+                if left <= 0:
+                    raise TimeoutError(f"{len(self.completed)}/{n_expected} requests done")
+                self._lock.wait(timeout=min(left, 1.0))
+
+    def close(self):
+        with self._lock:
+            self._closed = True
+            self._lock.notify_all()
+        self._dispatcher.join(timeout=10)
+
+    def replay(self, requests, timeout: float = 600.0):
+        """Submit requests at their arrival times (seconds from now), wait for all."""
+        base = self.now()
+        for r in sorted(requests, key=lambda r: r.arrival):
+            r.arrival += base
+            delay = r.arrival - self.now()
+            if delay > 0:
+                time.sleep(delay)
+            self.submit(r)
+        self.drain(len(requests), timeout)
+        return self.stats()
+
+    def stats(self):
+        ok = [r for r in self.completed if r.status == "done"]
+        lat = [1e3 * r.latency for r in ok]
+        svc = [1e3 * (r.done - r.admitted) for r in ok]
+        return {"requests": len(self.completed), "done": len(ok),
+                "rejected": sum(r.status == "rejected" for r in self.completed),
+                "errors": sum(r.status.startswith("error") for r in self.completed),
+                "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
+                "service_p50_ms": percentile(svc, 50), "service_p99_ms": percentile(svc, 99),
+                "max_concurrent": self.max_concurrent, "max_admitted_bytes": self.max_bytes,
+                "slots": self.slots, "budget_bytes": self.budget}
+
+
+class GpuExecutor:
+    """Runs a request through the C ABI on the slot's own CUDA stream."""
+
+    def __init__(self, idx, params, kernel, n_points, slots, max_nodes, copy_back=False):
+        import torch
+        from . import _lib as L
+        self.L, self.torch = L, torch
+        self.idx, self.params, self.kernel, self.n = idx, params, kernel, n_points
+        self.copy_back = copy_back
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        dev = "cuda"
+        self.grid = [torch.empty(max_nodes, device=dev) for _ in range(slots)]
+        self.dens = [torch.empty(n_points, device=dev) for _ in range(slots)]
+        self.ids = [torch.empty(n_points, dtype=torch.int32, device=dev) for _ in range(slots)]
+        self.sel = [torch.empty(n_points, dtype=torch.int32, device=dev) for _ in range(slots)]
+
+    def run(self, req: Request, slot: int):
+        L, torch = self.L, self.torch
+        st = self.streams[slot]
+        box = L.make_box(req.lo, req.hi)
+        G = int(req.dims[0]) * int(req.dims[1]) * int(req.dims[2])
+        grid = self.grid[slot][:G]
+        L.sf_kde_grid(self.idx, box, req.dims, self.kernel, self.params, grid, stream=st)
+        out = {"nodes": G}
+        if req.want_points:
+            cnt = L.sf_kde_points(self.idx, box, None, self.kernel, self.params, self.dens[slot],
+                                  self.ids[slot], stream=st)
+            nsel, t = L.sf_select(self.idx, self.dens[slot], self.ids[slot], cnt, self.n,
+                                  math.nan, req.select_pct, None, self.sel[slot], stream=st)
+            out.update(points=cnt, selected=nsel, threshold=t)
+        st.synchronize()
+        if self.copy_back:
+            out["grid"] = grid.cpu()
+            if req.want_points:
+                out["dens"] = self.dens[slot][:out["points"]].cpu()
+                out["sel"] = self.sel[slot][:out["selected"]].cpu()
+        return out
+
+
+def navigation_requests(n: int, rate: float, centre, seed: int, edges=(64, 96, 128, 192, 256),
+                        log_range=(-3.0, 0.0), step_decades=0.1):
+    """Seeded progressive-navigation stream: Poisson arrivals at `rate` per second;
+    the ROI scale walks in log10 space with Gaussian steps (reflected at the range
+    ends), the centre pans by up to half an edge per step; grid edges uniform in
+    `edges`. Cubic ROIs kept inside the unit cube."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    scale = log_range[1] - 0.5
+    c = np.array(centre, dtype=np.float64)
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        scale += rng.normal(0.0, step_decades)
+        lo_s, hi_s = log_range
+        if scale < lo_s:
+            scale = 2 * lo_s - scale
+        if scale > hi_s:
+            scale = 2 * hi_s - scale
+        e = 10.0 ** scale
+        c = c + (rng.random(3) - 0.5) * e
+        c = np.clip(c, e / 2, 1 - e / 2)
+        g = int(rng.choice(edges))
+        out.append(Request(rid=i, lo=tuple(c - e / 2), hi=tuple(c + e / 2), dims=(g, g, g),
+                           arrival=t))
+    return out

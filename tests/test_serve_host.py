@@ -1,0 +1,81 @@
+"""Host logic of the serving loop (admission, slots, memory budget, latency
+statistics) with a fake executor: CPU only."""
+import threading
+import time
+
+import pytest
+
+from paper_2601_20758_gb300 import serve
+
+
+class FakeExecutor:
+    def __init__(self, service_s=0.02):
+        self.service_s = service_s
+        self.lock = threading.Lock()
+        self.running = 0
+        self.max_running = 0
+        self.order = []
+
+    def run(self, req, slot):
+        with self.lock:
+            self.running += 1
+            self.max_running = max(self.max_running, self.running)
+            self.order.append(req.rid)
+        time.sleep(self.service_s)
+        with self.lock:
+            self.running -= 1
+        return {"slot": slot}
+
+
+def _reqs(n, dims=(16, 16, 16), gap=0.0):
+    return [serve.Request(rid=i, lo=(0, 0, 0), hi=(1, 1, 1), dims=dims, arrival=i * gap)
+            for i in range(n)]
+
+
+def test_slots_bound_concurrency_and_admission_is_fifo():
+    ex = FakeExecutor(0.02)
+    srv = serve.Server(ex, slots=3, mem_budget=1 << 40, n_points=1000)
+    try:
+        st = srv.replay(_reqs(12))
+    finally:
+        srv.close()
+    assert st["done"] == 12 and st["errors"] == 0
+    assert ex.max_running <= 3 and srv.max_concurrent == 3
+    assert ex.order == sorted(ex.order)          # admitted in arrival order
+    assert st["p99_ms"] >= st["p50_ms"] >= 20.0 * 0.9
+
+
+def test_memory_budget_limits_admission_and_rejects_oversize():
+    n_points = 1000
+    small = serve.Request(rid=0, lo=(0, 0, 0), hi=(1, 1, 1), dims=(32, 32, 32))
+    need = serve.estimate_bytes(small, n_points)
+    ex = FakeExecutor(0.02)
+    srv = serve.Server(ex, slots=8, mem_budget=2 * need + need // 2, n_points=n_points)
+    try:
+        reqs = [serve.Request(rid=i, lo=(0, 0, 0), hi=(1, 1, 1), dims=(32, 32, 32)) for i in range(6)]
+        huge = serve.Request(rid=99, lo=(0, 0, 0), hi=(1, 1, 1), dims=(512, 512, 512))
+        st = srv.replay(reqs + [huge])
+    finally:
+        srv.close()
+    assert st["done"] == 6 and st["rejected"] == 1
+    assert ex.max_running <= 2                   # two fit in the budget, never three
+    assert srv.max_bytes <= 2 * need + need // 2
+
+
+def test_navigation_stream_is_seeded_and_in_the_unit_cube():
+    a = serve.navigation_requests(200, rate=200.0, centre=(0.3, 0.4, 0.5), seed=5)
+    b = serve.navigation_requests(200, rate=200.0, centre=(0.3, 0.4, 0.5), seed=5)
+    assert [(r.lo, r.hi, r.dims, r.arrival) for r in a] == [(r.lo, r.hi, r.dims, r.arrival) for r in b]
+    for r in a:
+        e = r.hi[0] - r.lo[0]
+        assert 1e-3 * 0.999 <= e <= 1.0 + 1e-12
+        assert all(0.0 - 1e-12 <= v <= 1.0 + 1e-12 for v in r.lo + r.hi)
+        assert r.dims[0] in (64, 96, 128, 192, 256)
+    gaps = [y.arrival - x.arrival for x, y in zip(a, a[1:])]
+    assert sum(gaps) / len(gaps) == pytest.approx(1 / 200.0, rel=0.25)
+
+
+def test_percentile_nearest_rank():
+    assert serve.percentile([5, 1, 4, 2, 3], 50) == 3
+    assert serve.percentile([5, 1, 4, 2, 3], 99) == 5
+    assert serve.percentile([], 50) is None
