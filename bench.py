@@ -306,12 +306,9 @@ def main():
             kern[name]["per_roi_ms"] = [sum(per[r::N_ROI]) / max(1, len(per[r::N_ROI]))
                                         for r in range(N_ROI)] if len(per) >= N_ROI else per
     L.load().sf_kernel_timing_reset()
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = slowest_rank(elapsed_ms, world, dist, "cuda")
     ms_per_step = elapsed_ms / args.steps
-    value = pairs_step * args.steps * world / (elapsed_ms / 1e3) if pairs_step else None
+    value = whole_job_rate(pairs_step * args.steps, world, elapsed_ms / 1e3) if pairs_step else None
 
     # ---- roofline of the dominant kernel
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
@@ -382,6 +379,22 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def slowest_rank(elapsed, world, dist, device):
+    """The max over ranks of a timing (every rank gets it)."""
+    if world <= 1:
+        return elapsed
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Replicas: every rank processes the same units; the job's rate is all
+    ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds
 
 
 def percentile(sorted_vals, q):
@@ -490,11 +503,8 @@ def run_e2e(args, L, torch, xyz, boxes, p, pairs_step, stream, world, barrier, d
         step()
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-    return {"value": pairs_step * args.steps * world / el if pairs_step else None, "unit": UNIT,
+    el = slowest_rank(el, world, dist, "cuda")
+    return {"value": whole_job_rate(pairs_step * args.steps, world, el) if pairs_step else None, "unit": UNIT,
             "h2d_bytes_per_step": stats["h2d"], "d2h_bytes_per_step": stats["d2h"],
             "ms_per_step": 1e3 * el / args.steps}
 
