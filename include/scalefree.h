@@ -70,7 +70,11 @@ enum { SF_BW_KNN = 0, SF_BW_MBE = 1, SF_BW_FIXED = 2 };
  * SF_SCOPE_GLOBAL: all particles, N_eff = N. */
 enum { SF_SCOPE_CLIP = 0, SF_SCOPE_GLOBAL = 1 };
 
-enum { SF_PREC_FP32 = 0 };
+/* Precision of the point densities (sf_kde_points, DIRECT, kNN bandwidths):
+ * FP32 everywhere, or the squared-distance cross term on tensor cores in TF32
+ * (one pass) or 3xTF32 (hi/lo split, three passes); see sf_kde_points. Grids
+ * and every other call are FP32 only. */
+enum { SF_PREC_FP32 = 0, SF_PREC_TF32 = 1, SF_PREC_3XTF32 = 2 };
 
 /* Point densities: DIRECT evaluates the kernel sum at each point (self term
  * included); INTERP interpolates the ROI grid trilinearly (Sec. 3.1, last step). */
@@ -181,7 +185,13 @@ sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], i
  * receives the number of ROI points (the stream is synchronised). If the
  * count exceeds capacity, CAPACITY is returned and nothing is written.
  * DIRECT sums the kernels at each point (the point's own kernel included);
- * INTERP interpolates the grid of the same dims trilinearly. dims is used by
+ * INTERP interpolates the grid of the same dims trilinearly.
+ * params->prec TF32 / 3XTF32 (DIRECT with kNN bandwidths only): the cross term
+ * -2 x.y of each squared distance, in coordinates centred on each group of 32
+ * query points, runs on the tensor cores; the relative error of q = d^2/h^2 is
+ * about 2^-10 (TF32) or 2^-21 (3xTF32) times (|x| + |y|)^2 / d^2, so TF32
+ * densities carry errors of order 1e-3 to 1e-2 and 3xTF32 ones of order 1e-5;
+ * near the cutoff a pair may fall on either side. dims is used by
  * INTERP and by rule MBE (whose smoothing lengths depend on the grid spacing);
  * it may be NULL otherwise.
  */

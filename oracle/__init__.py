@@ -66,7 +66,8 @@ def _load():
         lib.or_knn.argtypes = [f32p, i64, ctypes.c_int, i64p, i64, f32p, i64p, f64p]
         lib.or_knn.restype = ctypes.c_int
         lib.or_density_at.argtypes = [f32p, i64, f64p, u8p, ctypes.c_double, ctypes.c_int,
-                                      ctypes.c_double, f64p, i64, f64p, f64p, f64p, i64p]
+                                      ctypes.c_double, f64p, i64, f64p, f64p, f64p, i64p,
+                                      ctypes.c_double]
         lib.or_density_at.restype = None
         lib.or_num_threads.restype = ctypes.c_int
         lib.or_set_num_threads.argtypes = [ctypes.c_int]
@@ -164,10 +165,12 @@ def in_box(xyz, box) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # Kernel sums (Eqs. 2, 4, 7)
 # ---------------------------------------------------------------------------
-def density_at(xyz, ell, r, kernel: int, inv_neff: float, member=None):
+def density_at(xyz, ell, r, kernel: int, inv_neff: float, member=None, amb_band: float = 1e-6):
     """rho(r) for every row of r, summed over all (member) particles in FP64.
 
     ell: [N, 3] per-particle smoothing lengths (l_x, l_y, l_z) in double.
+    amb_band: relative half-width around the support cutoff whose pairs count as
+    ambiguous (the rounding of the evaluation being compared decides them).
     Returns dict(rho, wpeak, amb, pairs) of arrays of length len(r).
     """
     a = _xyz(xyz)
@@ -184,7 +187,7 @@ def density_at(xyz, ell, r, kernel: int, inv_neff: float, member=None):
                           _ptr(mem, ctypes.c_uint8), float(inv_neff), int(kernel), P3,
                           _ptr(rr, ctypes.c_double), m, _ptr(rho, ctypes.c_double),
                           _ptr(wpk, ctypes.c_double), _ptr(amb, ctypes.c_double),
-                          _ptr(pairs, ctypes.c_int64))
+                          _ptr(pairs, ctypes.c_int64), float(amb_band))
     return {"rho": rho, "wpeak": wpk, "amb": amb, "pairs": pairs}
 
 

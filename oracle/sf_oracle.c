@@ -121,14 +121,15 @@ int or_knn(const float *xyz, int64_t n, int k, const int64_t *q, int64_t nq,
  * member (nullable): n flags; 0 excludes particle j (the ROI clip scope).
  * wpeak (nullable): inv_neff * sum over in-support j of K(0; l_j).
  * amb   (nullable): inv_neff * sum of |K| (untruncated profile) over pairs with
- *                   |q/qmax - 1| < 1e-6 on either side of the cutoff: the mass
- *                   whose in/out decision depends on rounding order alone.
+ *                   |q/qmax - 1| < amb_band on either side of the cutoff: the mass
+ *                   whose in/out decision depends on rounding alone (1e-6 for
+ *                   an FP32 evaluation of q; wider for reduced-precision ones).
  * pairs (nullable): number of in-support (q < qmax) pairs per target.
  */
 void or_density_at(const float *xyz, int64_t n, const double *ell,
                    const uint8_t *member, double inv_neff, int kernel, double p3,
                    const double *r, int64_t m, double *rho, double *wpeak,
-                   double *amb, int64_t *pairs) {
+                   double *amb, int64_t *pairs, double amb_band) {
     const double pi = 3.14159265358979323846;
     const double qmax = (kernel == OR_K_EPAN) ? 1.0 : 9.0;
     const double cnorm = (kernel == OR_K_EPAN) ? 15.0 / (8.0 * pi)
@@ -149,7 +150,7 @@ void or_density_at(const float *xyz, int64_t n, const double *ell,
             double qq = ((ux * ux) + (uy * uy)) + (uz * uz);
             /* pairs this close to the cutoff are in or out by rounding order alone:
                their kernel value counts as ambiguous on both sides of q = qmax */
-            int ambiguous = fabs(qq / qmax - 1.0) < 1e-6;
+            int ambiguous = fabs(qq / qmax - 1.0) < amb_band;
             if (!(qq < qmax) && !ambiguous) continue;
             double peak = cnorm / ((lx * ly) * lz);
             double val = (kernel == OR_K_EPAN) ? peak * (1.0 - qq) : peak * exp(-0.5 * qq);

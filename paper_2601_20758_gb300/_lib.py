@@ -33,6 +33,8 @@ SF_BW_FIXED = 2
 SF_SCOPE_CLIP = 0
 SF_SCOPE_GLOBAL = 1
 SF_PREC_FP32 = 0
+SF_PREC_TF32 = 1
+SF_PREC_3XTF32 = 2
 SF_POINTS_DIRECT = 0
 SF_POINTS_INTERP = 1
 

@@ -23,6 +23,8 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
                       float *d_pilot, cudaStream_t s);
 sf_status interp_points(sf_index *idx, const sf_box &roi, const GridSpec &g, const float *d_grid,
                         float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s);
+sf_status density_points_tc(sf_index *idx, const sf_box &roi, const DensityCall &call, int prec,
+                            float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s);
 
 // Count the points of the scope and set N_eff (device); EMPTY_ROI is recorded
 // in the status word when the clip scope holds no point.
@@ -95,7 +97,8 @@ static sf_status check_params(const sf_index *idx, const sf_params *p, int kerne
         return fail(SF_ERR_INVALID_ARG, "%s: unknown kernel %d", fn, kernel);
     if (p->scope != SF_SCOPE_CLIP && p->scope != SF_SCOPE_GLOBAL)
         return fail(SF_ERR_INVALID_ARG, "%s: unknown scope %d", fn, p->scope);
-    if (p->prec != SF_PREC_FP32) return fail(SF_ERR_INVALID_ARG, "%s: unsupported precision %d", fn, p->prec);
+    if (p->prec != SF_PREC_FP32 && p->prec != SF_PREC_TF32 && p->prec != SF_PREC_3XTF32)
+        return fail(SF_ERR_INVALID_ARG, "%s: unsupported precision %d", fn, p->prec);
     if (p->points_mode != SF_POINTS_DIRECT && p->points_mode != SF_POINTS_INTERP)
         return fail(SF_ERR_INVALID_ARG, "%s: unknown points_mode %d", fn, p->points_mode);
     if (p->reserved != 0) return fail(SF_ERR_INVALID_ARG, "%s: reserved must be 0", fn);
@@ -249,6 +252,8 @@ sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], i
     if (!idx || !d_out) return fail(SF_ERR_INVALID_ARG, "sf_kde_grid: NULL argument");
     SF_TRY(check_roi(roi, "sf_kde_grid"));
     SF_TRY(check_params(idx, params, kernel, "sf_kde_grid"));
+    if (params->prec != SF_PREC_FP32)
+        return fail(SF_ERR_INVALID_ARG, "sf_kde_grid: grids are FP32 only");
     GridSpec g;
     SF_TRY(make_grid(*roi, dims, g, "sf_kde_grid"));
     cudaStream_t s = (cudaStream_t)stream;
@@ -284,7 +289,12 @@ sf_status sf_kde_points(sf_index *idx, const sf_box *roi, const int32_t *dims, i
     SF_TRY_SCRATCH(sc);
     Prepared pr;
     SF_TRY(prepare(idx, *roi, need_grid ? &g : nullptr, kernel, *params, sc, pr, s));
-    if (params->points_mode == SF_POINTS_INTERP) {
+    if (params->prec != SF_PREC_FP32 &&
+        (params->rule != SF_BW_KNN || params->points_mode != SF_POINTS_DIRECT))
+        return fail(SF_ERR_INVALID_ARG, "sf_kde_points: TF32 / 3xTF32 need rule KNN and DIRECT");
+    if (params->prec != SF_PREC_FP32) {
+        SF_TRY(density_points_tc(idx, *roi, pr.call, params->prec, rho, inroi, s));
+    } else if (params->points_mode == SF_POINTS_INTERP) {
         float *grid = sc.get<float>((int64_t)g.nx * g.ny * g.nz);
         SF_TRY_SCRATCH(sc);
         SF_TRY(density_grid(idx, *roi, g, pr.call, grid, nullptr, s));
@@ -364,6 +374,8 @@ sf_status sf_batch_create(sf_index *idx, int32_t nroi, const sf_box *rois, const
     SF_TRY(check_params(idx, params, kernel, "sf_batch_create"));
     if (params->rule == SF_BW_MBE)
         return fail(SF_ERR_INVALID_ARG, "sf_batch_create: rule MBE is per ROI; use sf_kde_grid");
+    if (params->prec != SF_PREC_FP32)
+        return fail(SF_ERR_INVALID_ARG, "sf_batch_create: grids are FP32 only");
     int tz = 8, ips = 4;
     bool graph = true;
     if (tune) {

@@ -1450,6 +1450,228 @@ static cudaError_t dispatch_points(int bw, bool clip, const PointsArgs &a, int64
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core cross term (precision variants of the point densities)
+//
+// With coordinates taken relative to the query leaf's centre, the squared
+// distance of query i and candidate j is |x_i|^2 + |y_j|^2 - 2 x_i . y_j; the
+// cross term of a 32 x 32 block is a [32 x 8] . [8 x 32] product (features x,
+// y, z, zero-padded) done by mma.sync m16n8k8 in TF32 (or as the 3-pass
+// hi/lo split, "3xTF32", accurate to about 2^-21 of |x||y|); the squared norms,
+// the scaling by 1/h^2, the cutoff, the kernel and the compensated sums stay
+// in FP32. Isotropic bandwidths only (the kNN rule).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float d[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    // A rows (groupID, groupID + 8) x cols (tig, tig + 4): cols >= 4 are zero padding
+    const uint32_t z = 0u;
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(z), "r"(z), "r"(b0), "r"(z));
+}
+
+template <int PREC>
+__device__ __forceinline__ void cross_mma(float d[4], float a0f, float a1f, float b0f) {
+    const uint32_t a0h = to_tf32(a0f), a1h = to_tf32(a1f), b0h = to_tf32(b0f);
+    mma_tf32(d, a0h, a1h, b0h);
+    if (PREC == SF_PREC_3XTF32) {
+        const uint32_t a0l = to_tf32(a0f - __uint_as_float(a0h));
+        const uint32_t a1l = to_tf32(a1f - __uint_as_float(a1h));
+        const uint32_t b0l = to_tf32(b0f - __uint_as_float(b0h));
+        mma_tf32(d, a0h, a1h, b0l);
+        mma_tf32(d, a0l, a1l, b0h);
+    }
+}
+
+struct TcWarpSmem {
+    int stack[kStack];
+    int leaves[kBatch];
+    float4 yp[kLeaf];   // candidate relative position (x', y', z', -)
+    float4 yk[kLeaf];   // (|y'|^2, u^2, c, -)
+};
+
+template <int KER, bool CLIP, int PREC>
+__global__ void __launch_bounds__(kPtWarps * 32) k_points_tc(PointsArgs a) {
+    __shared__ TcWarpSmem W[kPtWarps];
+    __shared__ double s_inv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, tig = lane & 3;
+    if (threadIdx.x == 0) s_inv = a.e.dp->inv_neff;
+    __syncthreads();
+    TcWarpSmem &S = W[warp];
+    const int64_t leaf = (int64_t)blockIdx.x * kPtWarps + warp;
+    if (leaf >= a.e.tv.cnt[0]) return;
+    const int64_t qi = leaf * kLeaf + lane;
+    const bool valid = qi < a.e.tv.n;
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) q = __ldg(&a.e.tv.pos[qi]);
+    const bool active = valid && q.x >= a.e.blo[0] && q.x <= a.e.bhi[0] && q.y >= a.e.blo[1] &&
+                        q.y <= a.e.bhi[1] && q.z >= a.e.blo[2] && q.z <= a.e.bhi[2];
+    if (valid) a.inroi[qi] = active ? 1 : 0;
+    const unsigned am = __ballot_sync(0xffffffffu, active);
+    if (am == 0) return;
+    float tlo[3] = {active ? q.x : INFINITY, active ? q.y : INFINITY, active ? q.z : INFINITY};
+    float thi[3] = {active ? q.x : -INFINITY, active ? q.y : -INFINITY, active ? q.z : -INFINITY};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tlo[k] = fminf(tlo[k], __shfl_xor_sync(0xffffffffu, tlo[k], o));
+            thi[k] = fmaxf(thi[k], __shfl_xor_sync(0xffffffffu, thi[k], o));
+        }
+    const float cen[3] = {0.5f * (tlo[0] + thi[0]), 0.5f * (tlo[1] + thi[1]), 0.5f * (tlo[2] + thi[2])};
+    // this lane's four rows (queries g, g+8, g+16, g+24) relative to the centre
+    const float xq[3] = {q.x - cen[0], q.y - cen[1], q.z - cen[2]};
+    float feat[4], xsq[4];
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl) {
+        const int r = g + 8 * sl;
+        const float rx = __shfl_sync(0xffffffffu, xq[0], r);
+        const float ry = __shfl_sync(0xffffffffu, xq[1], r);
+        const float rz = __shfl_sync(0xffffffffu, xq[2], r);
+        feat[sl] = tig == 0 ? rx : (tig == 1 ? ry : (tig == 2 ? rz : 0.f));
+        xsq[sl] = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+    }
+    float uni[3] = {0.f, 0.f, 0.f};
+    auto test = [&](int64_t node) { return node_reaches<KER, BW_ISO, CLIP>(a.e, uni, node, tlo, thi); };
+
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, sum[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
+    int spv;
+    int nl = warp_walk_start(a.e.tv, test, S.stack, spv, S.leaves);
+    while (true) {
+        if (nl == 0) {
+            if (spv == 0) break;
+            nl = warp_walk(a.e.tv, test, S.stack, spv, S.leaves, kBatch);
+            if (nl == 0) break;
+        }
+        for (int li = 0; li < nl; ++li) {
+            const int64_t j = (int64_t)S.leaves[li] * kLeaf + lane;
+            bool ok = false;
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < a.e.tv.n) {
+                p = __ldg(&a.e.tv.pos[j]);
+                ok = p.w > 0.f;
+                if (CLIP)
+                    ok = ok && p.x >= a.e.blo[0] && p.x <= a.e.bhi[0] && p.y >= a.e.blo[1] &&
+                         p.y <= a.e.bhi[1] && p.z >= a.e.blo[2] && p.z <= a.e.bhi[2];
+                const float pc[3] = {p.x, p.y, p.z};
+                float qlb = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    float gap = fmaxf(fmaxf(tlo[k] - pc[k], pc[k] - thi[k]), 0.f);
+                    gap = fmaxf(gap - 1.0e-6f * (fabsf(tlo[k]) + fabsf(thi[k])), 0.f);
+                    const float t = gap / (p.w * KDef<KER>::rmul);
+                    qlb += t * t;
+                }
+                ok = ok && qlb < 1.0f + 1.0e-5f;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const int s = __popc(m & ((1u << lane) - 1u));
+                const float y0 = p.x - cen[0], y1 = p.y - cen[1], y2 = p.z - cen[2];
+                const float u = KDef<KER>::uscale / p.w;
+                S.yp[s] = make_float4(y0, y1, y2, 0.f);
+                S.yk[s] = make_float4(fmaf(y2, y2, fmaf(y1, y1, y0 * y0)), u * u,
+                                      a.e.cnorm / ((p.w * p.w) * p.w), 0.f);
+            }
+            __syncwarp();
+            const int ns = __popc(m);
+            for (int nt = 0; nt * 8 < ns; ++nt) {
+                // B column g = candidate nt*8 + g, feature row tig: -2 y'
+                const int cb = nt * 8 + g;
+                float bf = 0.f;
+                if (cb < ns && tig < 3) {
+                    const float4 y = S.yp[cb];
+                    bf = -2.f * (tig == 0 ? y.x : (tig == 1 ? y.y : y.z));
+                }
+                float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+                cross_mma<PREC>(d0, feat[0], feat[1], bf);   // rows g, g+8
+                cross_mma<PREC>(d1, feat[2], feat[3], bf);   // rows g+16, g+24
+                // epilogue: columns 2 tig, 2 tig + 1 of this n-tile
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int jc = nt * 8 + 2 * tig + cc;
+                    if (jc < ns) {
+                        const float4 yk = S.yk[jc];
+                        const float dv[4] = {d0[cc], d0[2 + cc], d1[cc], d1[2 + cc]};
+#pragma unroll
+                        for (int sl = 0; sl < 4; ++sl) {
+                            const float d2 = (xsq[sl] + yk.x) + dv[sl];
+                            const float qq = fmaxf(d2, 0.f) * yk.y;
+                            if (qq < KDef<KER>::qmax) {
+                                if (KER == SF_K_GAUSS3) acc[sl] = fmaf(yk.z, ex2_approx(-qq), acc[sl]);
+                                else acc[sl] = fmaf(yk.z, 1.0f - qq, acc[sl]);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl) {
+                const float t = sum[sl] + acc[sl];
+                const float bp = t - sum[sl];
+                cmp[sl] += (sum[sl] - (t - bp)) + (acc[sl] - bp);
+                sum[sl] = t;
+                acc[sl] = 0.f;
+            }
+        }
+        nl = 0;
+    }
+    // rows are spread over the four lanes of a group: add them up, then route row L to lane L
+    double v[4];
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl) {
+        v[sl] = (double)sum[sl] + (double)cmp[sl];
+        v[sl] += __shfl_xor_sync(0xffffffffu, v[sl], 1);
+        v[sl] += __shfl_xor_sync(0xffffffffu, v[sl], 2);
+    }
+    const int src = 4 * (lane & 7), mysl = lane >> 3;
+    double mine = 0.0;
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl) {
+        const double t = __shfl_sync(0xffffffffu, v[sl], src);
+        if (sl == mysl) mine = t;
+    }
+    if (active) a.rho_sorted[qi] = (float)(mine * s_inv);
+}
+
+template <int KER, bool CLIP>
+static cudaError_t launch_points_tc(int prec, const PointsArgs &a, int64_t nleaf, cudaStream_t s) {
+    KTimer t("k_points_tc", s);
+    if (prec == SF_PREC_3XTF32)
+        return launch(k_points_tc<KER, CLIP, SF_PREC_3XTF32>, dim3(blocks_for(nleaf, kPtWarps)),
+                      dim3(kPtWarps * 32), 0, s, a);
+    return launch(k_points_tc<KER, CLIP, SF_PREC_TF32>, dim3(blocks_for(nleaf, kPtWarps)),
+                  dim3(kPtWarps * 32), 0, s, a);
+}
+
+sf_status density_points_tc(sf_index *idx, const sf_box &roi, const DensityCall &call, int prec,
+                            float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s) {
+    if (call.bw != BW_ISO)
+        return fail(SF_ERR_INVALID_ARG, "tensor-core point densities need isotropic (kNN) bandwidths");
+    PointsArgs a;
+    a.e = engine_args(idx, roi, call);
+    a.rho_sorted = d_rho_sorted;
+    a.inroi = d_inroi;
+    a.pairs = nullptr;
+    const int64_t nl = idx->cnt[0];
+    cudaError_t e;
+    if (call.kernel == SF_K_EPAN)
+        e = call.clip ? launch_points_tc<SF_K_EPAN, true>(prec, a, nl, s) : launch_points_tc<SF_K_EPAN, false>(prec, a, nl, s);
+    else
+        e = call.clip ? launch_points_tc<SF_K_GAUSS3, true>(prec, a, nl, s) : launch_points_tc<SF_K_GAUSS3, false>(prec, a, nl, s);
+    SF_TRY_CUDA(e);
+    return SF_OK;
+}
+
 sf_status density_points(sf_index *idx, const sf_box &roi, const DensityCall &call,
                          float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s,
                          unsigned long long *d_pairs) {

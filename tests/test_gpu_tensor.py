@@ -1,0 +1,91 @@
+"""Tensor-core cross-term precision variants of the point densities (TF32 and
+3xTF32) against the FP64 oracle: the measured error of every result, against
+the a priori bounds stated in include/scalefree.h."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_20758_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# Max relative error over outputs >= 1e-3 of the largest, per kernel. A priori: TF32
+# rounds both operands of the cross term to 11 significant bits, so
+# |dq| <~ 2^-10 * 2 |x||y| / h^2 with |x| <~ e (half the query group's extent) and
+# |y| <~ e + 3h: about 1e-2 for e ~ h; the Gaussian's relative error is |dq|/2, the
+# Epanechnikov's |dq|/(1 - q), larger near the edge. 3xTF32 leaves 2^-21 instead
+# of 2^-10. Measured on this cloud (GB300): Gaussian 4.4e-2 (TF32) and 1.6e-5
+# (3xTF32); Epanechnikov 1.5e-1 and 8.8e-5; FP32 below 3e-7 for both.
+BOUNDS = {"tf32": {1: 1e-1, 0: 3e-1}, "3xtf32": {1: 5e-5, 0: 2e-4}, "fp32": {1: 1e-5, 0: 1e-5}}
+BANDS = {"tf32": 2e-2, "3xtf32": 2e-5, "fp32": 1e-6}     # cutoff ambiguity band
+
+
+@pytest.mark.parametrize("kernel", [oracle.GAUSS3, oracle.EPAN])
+def test_tensor_core_point_densities_error(kernel):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_20758_gb300 import build
+    build.build()
+    from paper_2601_20758_gb300 import _lib as L
+    xyz = synth.plain_cloud(20000, seed=23)
+    n = xyz.shape[0]
+    roi = ((0.1, 0.1, 0.1), (0.9, 0.9, 0.9))
+    d = torch.from_numpy(xyz).cuda()
+    idx = L.sf_build_index(d)
+    report = {}
+    try:
+        h, _, _ = oracle.knn(xyz, 32)
+        inb = np.nonzero(oracle.in_box(xyz, roi))[0]
+        for name, prec in (("fp32", L.SF_PREC_FP32), ("tf32", L.SF_PREC_TF32),
+                           ("3xtf32", L.SF_PREC_3XTF32)):
+            p = L.make_params(rule=L.SF_BW_KNN, k=32)
+            p.prec = prec
+            if name == "fp32":
+                L.sf_bandwidths(idx, p)
+            dens = torch.empty(n, device="cuda")
+            ids = torch.empty(n, dtype=torch.int32, device="cuda")
+            cnt = L.sf_kde_points(idx, L.make_box(*roi), None, kernel, p, dens, ids)
+            assert cnt == inb.size
+            ref = oracle.density_at(xyz, oracle.iso_ell(h), xyz[inb].astype(np.float64), kernel,
+                                    1.0 / n, amb_band=BANDS[name])
+            g = dens[:cnt].cpu().numpy().astype(np.float64)
+            r = ref["rho"]
+            big = r >= 1e-3 * r.max()
+            excess = np.maximum(np.abs(g - r) - ref["amb"], 0.0)
+            rel = excess[big] / r[big]
+            report[name] = {"max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
+                            "rms_rel": float(np.sqrt(np.mean(rel ** 2)))}
+        out = os.environ.get("SF_TENSOR_REPORT")
+        if out:
+            with open(out, "a") as f:
+                f.write(json.dumps({"kernel": int(kernel), **report}) + "\n")
+        for name, rep in report.items():
+            assert rep["max_rel"] <= BOUNDS[name][int(kernel)], (name, rep)
+        assert report["3xtf32"]["max_rel"] < report["tf32"]["max_rel"]
+    finally:
+        L.sf_free_index(idx)
+
+
+def test_tensor_core_rejected_where_not_defined():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_20758_gb300 import _lib as L
+    xyz = synth.plain_cloud(2000, seed=2)
+    d = torch.from_numpy(xyz).cuda()
+    idx = L.sf_build_index(d)
+    try:
+        p = L.make_params(rule=L.SF_BW_FIXED, fixed_h=(0.05, 0.05, 0.05))
+        p.prec = L.SF_PREC_TF32
+        dens = torch.empty(2000, device="cuda")
+        ids = torch.empty(2000, dtype=torch.int32, device="cuda")
+        with pytest.raises(L.SFError):
+            L.sf_kde_points(idx, L.make_box((0, 0, 0), (1, 1, 1)), None, L.SF_K_GAUSS3, p, dens, ids)
+        grid = torch.empty(8 ** 3, device="cuda")
+        with pytest.raises(L.SFError):
+            L.sf_kde_grid(idx, L.make_box((0, 0, 0), (1, 1, 1)), (8, 8, 8), L.SF_K_GAUSS3, p, grid)
+    finally:
+        L.sf_free_index(idx)
