@@ -31,7 +31,7 @@ constexpr int kKnnWarps = 4;
 constexpr int kNB = 32;        // histogram bins per lane
 constexpr int kBand = 16;      // band buffer per lane
 constexpr int kCand = 64;      // candidate leaves per walk batch
-constexpr int kCache = 8192;   // candidate points per warp buffer (global)
+constexpr int kCache = 32768;  // candidate points per warp buffer (global)
 constexpr int kKStack = 32 * kMaxLevels;
 constexpr float kDelta = 2.0e-6f;
 
