@@ -13,12 +13,13 @@
 //  2. candidates: the index walk keeps the leaves within that radius of at
 //     least one lane's point; their points inside the warp's envelope box are
 //     compacted once into a per-warp buffer in global memory (L2-resident);
-//  3. histogram pass over the buffer: per lane, 32 bins of FP32 d2, the bin
-//     holding the k-th is found;
+//  3. histogram while collecting: per lane, 32 bins of FP32 d2 over [0, T];
+//     the bin holding the k-th is found;
 //  4. band pass: points clearly below the bin are in; the few whose FP32 d2 lies
 //     within a relative 2e-6 of the bin are re-evaluated in FP64 (no FMA
 //     contraction) and ranked by (d2, original index). If a band overflows its
-//     buffer the bin is split again; at FP32 resolution (exact duplicates) the
+//     buffer the bin is split again (the band pass has already binned the
+//     bracket for that round); at FP32 resolution (exact duplicates) the
 //     remaining members are extracted one by one.
 // FP32 d2 carries a relative error below 5 * 2^-24, so the 2e-6 margins make
 // every in/out decision outside the band exact. If a warp's candidates exceed
@@ -195,12 +196,15 @@ struct KnnWarp {
         }
     }
 
-    // Fill the global candidate buffer once.
-    __device__ void collect() {
+    // Fill the global candidate buffer once; fn(n) sees each staged chunk
+    // S.pts[0..n) on the way (all lanes together).
+    template <typename Fn>
+    __device__ void collect(Fn fn) {
         const int lane = threadIdx.x & 31;
         ncache = 0;
         overflow = false;
         walk_points([&](int n) {
+            fn(n);
             if (ncache + n <= kCache) {
                 if (lane < n) cache[ncache + lane] = S.pts[lane];
             } else {
@@ -336,10 +340,25 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
             W.env_hi[d] = hi3[d];
         }
     }
-    W.collect();
+    // first histogram (32 bins over [0, T]) while the candidates are collected
+    clear_hist();
+    {
+        const float inv0 = (valid && T > 0.f) ? (float)kNB / T : 0.f;
+        const float t_a = valid ? T : -INFINITY;
+        W.collect([&](int n) {
+            for (int t = 0; t < n; ++t) {
+                const float4 p = S.pts[t];
+                const float d = d2_f32(q, p);
+                if (d <= t_a && __float_as_uint(p.w) != qid)
+                    S.hist[min(kNB - 1, (int)(d * inv0))][lane] += 1;
+            }
+            __syncwarp();
+        });
+    }
 
-    // ---- 3./4. histogram and band passes, refined until the band fits
+    // ---- 3./4. band passes; each also bins the band's bracket for a further round
     float lo_e = 0.f, hi_e = valid ? T : 0.f;
+    int below = 0;               // candidates with d2 < lo_e
     bool done = !valid;
     int need = 0;
     double kth = 0.0;
@@ -348,21 +367,8 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
     int nb_below = 0;
     for (int round = 0; round < 8; ++round) {
         if (!__any_sync(0xffffffffu, !done && !extract)) break;
-        clear_hist();
-        const float width = hi_e - lo_e;
-        const float inv = width > 0.f ? (float)kNB / width : 0.f;
         const bool act = !done && !extract;
-        const float lo_a = act ? lo_e : INFINITY;   // inactive lanes skip cheaply
-        const float hi_a = act ? hi_e : -INFINITY;
-        int below = 0;
-        W.each([&](float4 p) {
-            const float d = d2_f32(q, p);
-            if (d <= hi_a && __float_as_uint(p.w) != qid) {
-                if (d < lo_a) ++below;
-                else S.hist[min(kNB - 1, (int)((d - lo_a) * inv))][lane] += 1;
-            }
-        });
-        __syncwarp();
+        const float width = hi_e - lo_e;
         float e_lo = lo_e, e_hi = hi_e;
         if (act) {
             int cum = below, b = 0;
@@ -376,21 +382,27 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
             band_lo = e_lo * (1.0f - kDelta);
             band_hi = e_hi * (1.0f + kDelta);
         }
+        clear_hist();
         const float bhi_a = act ? band_hi : -INFINITY;
-        int nbelow = 0, nband = 0;
+        const float sub_w = e_hi - e_lo;
+        const float sub_inv = sub_w > 0.f ? (float)kNB / sub_w : 0.f;
+        int nbelow = 0, nband = 0, below_next = 0;
         W.each([&](float4 p) {
             const float d = d2_f32(q, p);
             if (d <= bhi_a) {
                 const uint32_t id = __float_as_uint(p.w);
                 if (id != qid) {
-                    if (d < band_lo) ++nbelow;
-                    else {
+                    if (d < band_lo) {
+                        ++nbelow;
+                    } else {
                         if (nband < kBand) {
                             S.bd[nband][lane] = d2_f64(q, p);
                             S.bi[nband][lane] = id;
                         }
                         ++nband;
                     }
+                    if (d < e_lo) ++below_next;
+                    else if (d <= e_hi) S.hist[min(kNB - 1, (int)((d - e_lo) * sub_inv))][lane] += 1;
                 }
             }
         });
@@ -417,8 +429,9 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
             } else if (round == 7 || !(e_hi - e_lo > 4.0f * kDelta * e_hi)) {
                 extract = true;  // bin cannot shrink further (or out of rounds)
             } else {
-                lo_e = e_lo;
+                lo_e = e_lo;     // the band pass already binned [e_lo, e_hi]
                 hi_e = e_hi;
+                below = below_next;
             }
         }
         __syncwarp();
