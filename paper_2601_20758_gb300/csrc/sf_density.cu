@@ -225,16 +225,16 @@ struct TileGeom {
     float tlo[3], thi[3], sp3[3];
 };
 
-template <int TZ>
+template <int TZ, int WX = kTileX, int WY = kTileY>
 __device__ __forceinline__ void tile_origin(const RoiDesc &r, int tile, int &gx0, int &gy0, int &gz0,
                                             int nv[3]) {
     const int tix = tile % r.tiles_x, tiy = (tile / r.tiles_x) % r.tiles_y,
               tiz = tile / (r.tiles_x * r.tiles_y);
-    gx0 = tix * kTileX;
-    gy0 = tiy * kTileY;
+    gx0 = tix * WX;
+    gy0 = tiy * WY;
     gz0 = tiz * TZ;
-    nv[0] = min(kTileX, r.nx - gx0);
-    nv[1] = min(kTileY, r.ny - gy0);
+    nv[0] = min(WX, r.nx - gx0);
+    nv[1] = min(WY, r.ny - gy0);
     nv[2] = min(TZ, r.nz - gz0);
 }
 
@@ -589,6 +589,7 @@ struct MrArgs {
 };
 
 constexpr int kWalkWarps = 8;
+constexpr int kWX = 8, kWY = 4;  // node tile of one warp in the split pipeline (x, y)
 
 struct WalkWarpSmem {
     int stack[kStack];
@@ -609,7 +610,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mr_walk(MrArgs a, uint32_t 
     if (lane == 0) set_roi_engine(S.e, a.e, r);
     __syncwarp();
     int gx0, gy0, gz0, nv[3];
-    tile_origin<TZ>(r, gt - r.tile_base, gx0, gy0, gz0, nv);
+    tile_origin<TZ, kWX, kWY>(r, gt - r.tile_base, gx0, gy0, gz0, nv);
     float tlo[3], thi[3];
     tlo[0] = r.axis[gx0].x;
     thi[0] = r.axis[gx0 + nv[0] - 1].x;
@@ -654,68 +655,248 @@ __global__ void k_grid_items(const uint32_t *__restrict__ cnt, const uint32_t *_
         items[ioff[t] + i] = make_int4(t, (int)(b + i * lpw), (int)(b + min(n, (i + 1) * lpw)), 0);
 }
 
+// Shared memory of one warp of the split pipeline: its 8 x 4 x TZ node tile.
+template <int TZ>
+struct WTileSmem {
+    float2 tx[kLeaf][kWX];   // Gauss: (c e^{-qx'}, qx'); Epan: (qx', -)
+    float2 ty[kLeaf][kWY];   // Gauss: (e^{-qy'}, qy');   Epan: (qy', -)
+    float2 tz[kLeaf][TZ];    // Gauss: (e^{-qz'}, qmax - qz'); Epan: (c (1 - qz'), -)
+    float4 sp[kLeaf];        // staged (x, y, z, c)
+    float4 su[kLeaf];        // staged (u_x, u_y, u_z, -)
+    int2 sf[kLeaf];          // footprint: x0|x1<<8|y0<<16|y1<<24, z0|z1<<8
+    float2 axt[kWX + kWY + TZ];
+    float uni[3];
+    EngineArgs e;
+    RoiDesc roi;
+};
+
+// Persistent warps: each takes (ROI, tile, leaf range) items from a counter and
+// sums them into the item's partial grid. No block barriers: a warp owns its
+// tile, its staging and its tables.
 template <int KER, int BW, bool CLIP, bool CNT, int TZ>
-__global__ void __launch_bounds__(kGridThreads, 3)
+__global__ void __launch_bounds__(kGridThreads)
     k_mr_work(MrArgs a, const int4 *__restrict__ items, const uint32_t *__restrict__ n_items,
               const int *__restrict__ list, double *__restrict__ part, unsigned int *next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GridSmemT<TZ> &S = *reinterpret_cast<GridSmemT<TZ> *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WTileSmem<TZ> &S = reinterpret_cast<WTileSmem<TZ> *>(smem_raw)[warp];
+    const int cx = lane & (kWX - 1), cy = lane / kWX;
     const uint32_t nitems = *n_items;
     unsigned long long npairs = 0;
     int cur_roi = -1;
     while (true) {
-        if (tid == 0) S.item = (int)atomicAdd(next, 1u);
-        __syncthreads();
-        const int item = S.item;
-        if ((uint32_t)item >= nitems) break;
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(next, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= nitems) break;
         const int4 it = items[item];
         const int ri = a.tile_roi[it.x];
-        if (ri != cur_roi) {  // uniform across the block
-            if (tid == 0) {
+        if (ri != cur_roi) {
+            if (lane == 0) {
                 S.roi = a.rois[ri];
                 set_roi_engine(S.e, a.e, S.roi);
             }
             cur_roi = ri;
-            __syncthreads();
+            __syncwarp();
         }
-        const TileGeom g = tile_setup<TZ>(S, it.x - S.roi.tile_base);
+        const EngineArgs &E = S.e;
+        const RoiDesc &r = S.roi;
+        // ---- the tile's node coordinates
+        TileGeom g;
+        tile_origin<TZ, kWX, kWY>(r, it.x - r.tile_base, g.gx0, g.gy0, g.gz0, g.nv);
+        if (lane < kWX + kWY + TZ) {
+            float2 v = make_float2(0.f, 0.f);
+            if (lane < kWX) {
+                if (lane < g.nv[0]) v = r.axis[g.gx0 + lane];
+            } else if (lane < kWX + kWY) {
+                const int j = lane - kWX;
+                if (j < g.nv[1]) v = r.axis[r.nx + g.gy0 + j];
+            } else {
+                const int j = lane - kWX - kWY;
+                if (j < g.nv[2]) v = r.axis[r.nx + r.ny + g.gz0 + j];
+            }
+            S.axt[lane] = v;
+        }
+        if (lane == 0) {
+            S.uni[0] = E.dp->ell_uniform[0];
+            S.uni[1] = E.dp->ell_uniform[1];
+            S.uni[2] = E.dp->ell_uniform[2];
+        }
+        __syncwarp();
+        {
+            const int off[3] = {0, kWX, kWX + kWY};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                g.tlo[k] = S.axt[off[k]].x;
+                g.thi[k] = S.axt[off[k] + g.nv[k] - 1].x;
+                g.sp3[k] = g.nv[k] > 1 ? (S.axt[off[k] + 1].x - S.axt[off[k]].x) : 1.f;
+            }
+        }
         float acc[TZ], sum[TZ], cmp[TZ];
 #pragma unroll
         for (int k = 0; k < TZ; ++k) acc[k] = sum[k] = cmp[k] = 0.f;
         unsigned long long np = 0;
-        for (int lb = it.y; lb < it.z; lb += kStage / kLeaf) {
-            grid_chunk<KER, BW, CLIP, CNT, TZ>(S, g, list + lb, min(kStage / kLeaf, it.z - lb), acc, np);
+        for (int lb = it.y; lb < it.z; ++lb) {
+            // ---- one candidate leaf: refine (footprint in this tile, clip) and stage
+            const int64_t i = (int64_t)list[lb] * kLeaf + lane;
+            bool acc_pt = false;
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            float l[3] = {0.f, 0.f, 0.f};
+            int2 fp = make_int2(0, 0);
+            if (i < E.tv.n) {
+                p = __ldg(&E.tv.pos[i]);
+                point_ell<BW>(E, S.uni, i, p, l);
+                acc_pt = l[0] > 0.f && l[1] > 0.f && l[2] > 0.f;
+                if (CLIP)
+                    acc_pt = acc_pt && p.x >= E.blo[0] && p.x <= E.bhi[0] && p.y >= E.blo[1] &&
+                             p.y <= E.bhi[1] && p.z >= E.blo[2] && p.z <= E.bhi[2];
+                const float pc[3] = {p.x, p.y, p.z};
+                int f0[3], f1[3];
+                float qlb = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float R = l[k] * KDef<KER>::rmul;
+                    if (g.sp3[k] > 0.f) {
+                        const float a0 = fminf(fmaxf(ceilf((pc[k] - R - g.tlo[k]) / g.sp3[k]) - 1.f, -1.f), 64.f);
+                        const float a1 = fminf(fmaxf(floorf((pc[k] + R - g.tlo[k]) / g.sp3[k]) + 1.f, -1.f), 64.f);
+                        f0[k] = max(0, (int)a0);
+                        f1[k] = min(g.nv[k] - 1, (int)a1);
+                    } else {
+                        f0[k] = 0;
+                        f1[k] = g.nv[k] - 1;
+                    }
+                    if (f0[k] > f1[k]) acc_pt = false;
+                    float gap = fmaxf(fmaxf(g.tlo[k] - pc[k], pc[k] - g.thi[k]), 0.f);
+                    gap = fmaxf(gap - 1.0e-6f * (fabsf(g.tlo[k]) + fabsf(g.thi[k])), 0.f);
+                    const float t = gap / R;
+                    qlb += t * t;
+                }
+                if (!(qlb < 1.0f + 1.0e-5f)) acc_pt = false;
+                if (acc_pt) {
+                    fp.x = f0[0] | (f1[0] << 8) | (f0[1] << 16) | (f1[1] << 24);
+                    fp.y = f0[2] | (f1[2] << 8);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, acc_pt);
+            const int ns = __popc(bal);
+            if (ns == 0) continue;  // warp-uniform
+            if (acc_pt) {
+                const int s = __popc(bal & ((1u << lane) - 1u));
+                S.sp[s] = make_float4(p.x, p.y, p.z, E.cnorm / ((l[0] * l[1]) * l[2]));
+                S.su[s] = make_float4(KDef<KER>::uscale / l[0], KDef<KER>::uscale / l[1],
+                                      KDef<KER>::uscale / l[2], 0.f);
+                S.sf[s] = fp;
+            }
+            __syncwarp();
+            // ---- per-axis tables, footprint entries only
+            constexpr int kEnt = kWX + kWY + TZ;
+            for (int e = lane; e < ns * kEnt; e += 32) {
+                const int s = e / kEnt;
+                const int j = e - s * kEnt;
+                const int2 F = S.sf[s];
+                int axis, ii, lo_i, hi_i;
+                if (j < kWX) {
+                    axis = 0; ii = j; lo_i = F.x & 255; hi_i = (F.x >> 8) & 255;
+                } else if (j < kWX + kWY) {
+                    axis = 1; ii = j - kWX; lo_i = (F.x >> 16) & 255; hi_i = (F.x >> 24) & 255;
+                } else {
+                    axis = 2; ii = j - kWX - kWY; lo_i = F.y & 255; hi_i = (F.y >> 8) & 255;
+                }
+                if (ii < lo_i || ii > hi_i) continue;
+                const float4 P = S.sp[s];
+                const float4 U = S.su[s];
+                const float pc = axis == 0 ? P.x : (axis == 1 ? P.y : P.z);
+                const float u = axis == 0 ? U.x : (axis == 1 ? U.y : U.z);
+                const float2 nc = S.axt[j];
+                const float d = (nc.x - pc) + nc.y;
+                const float t = d * u;
+                const float q = t * t;
+                const bool sup = q < KDef<KER>::qmax;
+                float2 v;
+                if (KER == SF_K_GAUSS3) {
+                    const float w = sup ? ex2_approx(-q) : 0.f;
+                    if (axis == 0) v = make_float2(w * P.w, sup ? q : kBig);
+                    else if (axis == 1) v = make_float2(w, sup ? q : kBig);
+                    else v = make_float2(w, sup ? KDef<KER>::qmax - q : -1.f);
+                } else {
+                    if (axis < 2) v = make_float2(sup ? q : kBig, 0.f);
+                    else v = make_float2(sup ? P.w * (1.0f - q) : -kBig, 0.f);
+                }
+                if (axis == 0) S.tx[s][ii] = v;
+                else if (axis == 1) S.ty[s][ii] = v;
+                else S.tz[s][ii] = v;
+            }
+            __syncwarp();
+            // ---- accumulate: lane owns column (cx, cy) and TZ nodes in z
+            for (int s = 0; s < ns; ++s) {
+                const int2 F = S.sf[s];
+                const int x0 = F.x & 255, x1 = (F.x >> 8) & 255;
+                const int y0 = (F.x >> 16) & 255, y1 = (F.x >> 24) & 255;
+                const int z0 = F.y & 255, z1 = (F.y >> 8) & 255;
+                const bool in = cx >= x0 && cx <= x1 && cy >= y0 && cy <= y1;
+                float2 ex = KER == SF_K_GAUSS3 ? make_float2(0.f, kBig) : make_float2(kBig, 0.f);
+                float2 ey = ex;
+                if (in) {
+                    ex = S.tx[s][cx];
+                    ey = S.ty[s][cy];
+                }
+                if (KER == SF_K_GAUSS3) {
+                    const float bse = ex.x * ey.x;
+                    const float qij = ex.y + ey.y;
+#pragma unroll
+                    for (int k = 0; k < TZ; ++k) {
+                        if (k >= z0 && k <= z1) {
+                            const float2 ez = S.tz[s][k];
+                            if (qij < ez.y) {
+                                acc[k] = fmaf(bse, ez.x, acc[k]);
+                                if (CNT) ++np;
+                            }
+                        }
+                    }
+                } else {
+                    const float b = S.sp[s].w * (ex.x + ey.x);
+#pragma unroll
+                    for (int k = 0; k < TZ; ++k) {
+                        if (k >= z0 && k <= z1) {
+                            const float t = S.tz[s][k].x - b;
+                            acc[k] += fmaxf(t, 0.f);
+                            if (CNT) np += (t > 0.f);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
             fold<TZ>(acc, sum, cmp);
         }
         if (CNT && cx < g.nv[0] && cy < g.nv[1]) npairs += np;
-        double *o = part + ((int64_t)item * kGridThreads + tid) * TZ;
+        double *o = part + ((int64_t)item * 32 + lane) * TZ;
 #pragma unroll
         for (int k = 0; k < TZ; ++k) o[k] = (double)sum[k] + (double)cmp[k];
     }
     if (CNT) count_pairs_out(a.pairs, npairs);
 }
 
-// Per (ROI, tile): sum the items' partial grids in item order, scale, write, and the tile's mass.
+// One warp per (ROI, tile): sum the items' partial grids in item order, scale,
+// write, and the tile's mass.
 template <int TZ>
 __global__ void __launch_bounds__(kGridThreads) k_mr_reduce(MrArgs a, const uint32_t *__restrict__ ic,
                                                             const uint32_t *__restrict__ ioff,
                                                             const double *__restrict__ part) {
-    __shared__ double red[kGridThreads / 32];
-    const int gt = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
+    const int lane = threadIdx.x & 31;
+    const int gt = blockIdx.x * (kGridThreads / 32) + (threadIdx.x >> 5);
+    if (gt >= a.ntiles) return;
+    const int cx = lane & (kWX - 1), cy = lane / kWX;
     const RoiDesc &r = a.rois[a.tile_roi[gt]];
     const int tile = gt - r.tile_base;
     int gx0, gy0, gz0, nv[3];
-    tile_origin<TZ>(r, tile, gx0, gy0, gz0, nv);
+    tile_origin<TZ, kWX, kWY>(r, tile, gx0, gy0, gz0, nv);
     const double inv_neff = r.dp->inv_neff;
     double v[TZ];
 #pragma unroll
     for (int k = 0; k < TZ; ++k) v[k] = 0.0;
     const uint32_t i0 = ioff[gt], ni = ic[gt];
     for (uint32_t i = 0; i < ni; ++i) {
-        const double *pp = part + ((int64_t)(i0 + i) * kGridThreads + tid) * TZ;
+        const double *pp = part + ((int64_t)(i0 + i) * 32 + lane) * TZ;
 #pragma unroll
         for (int k = 0; k < TZ; ++k) v[k] += pp[k];
     }
@@ -734,13 +915,7 @@ __global__ void __launch_bounds__(kGridThreads) k_mr_reduce(MrArgs a, const uint
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, o);
-    if (lane == 0) red[warp] = msum;
-    __syncthreads();
-    if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kGridThreads / 32; ++w) t += red[w];
-        r.mass_part[tile] = t;
-    }
+    if (lane == 0) r.mass_part[tile] = msum;
 }
 
 __global__ void k_mass_final(const double *__restrict__ part, int64_t n, double cell,
@@ -828,9 +1003,14 @@ static sf_status mr_count(const MrArgs &a, uint32_t *cnt, uint32_t *off, uint32_
     return SF_OK;
 }
 
+template <int TZ>
+static size_t mr_work_smem() {
+    return sizeof(WTileSmem<TZ>) * (kGridThreads / 32);
+}
+
 template <int KER, int BW, bool CLIP, bool CNT, int TZ>
 static sf_status mr_work_attr(int *per_sm) {
-    const size_t smem = sizeof(GridSmemT<TZ>);
+    const size_t smem = mr_work_smem<TZ>();
     static bool attr = false;
     if (!attr) {
         SF_TRY_CUDA(cudaFuncSetAttribute(k_mr_work<KER, BW, CLIP, CNT, TZ>,
@@ -870,10 +1050,10 @@ static sf_status mr_exec(const MrArgs &a, const MrBuffers &b, cudaStream_t s) {
     {
         KTimer t(CNT ? "k_grid_work_count" : "k_grid_work", s);
         SF_TRY_CUDA(launch(k_mr_work<KER, BW, CLIP, CNT, TZ>, dim3((unsigned)b.slots), dim3(kGridThreads),
-                           sizeof(GridSmemT<TZ>), s, a, (const int4 *)b.items,
+                           mr_work_smem<TZ>(), s, a, (const int4 *)b.items,
                            (const uint32_t *)(b.tot + 1), (const int *)b.list, b.part, b.next));
     }
-    SF_TRY_CUDA(launch(k_mr_reduce<TZ>, dim3(a.ntiles), dim3(kGridThreads), 0, s, a,
+    SF_TRY_CUDA(launch(k_mr_reduce<TZ>, dim3(blocks_for(a.ntiles, kGridThreads / 32)), dim3(kGridThreads), 0, s, a,
                        (const uint32_t *)b.ic, (const uint32_t *)b.ioff, (const double *)b.part));
     return SF_OK;
 }
@@ -886,10 +1066,11 @@ static sf_status mr_plan(const MrArgs &a, uint32_t total, int items_per_slot, Mr
     SF_TRY_CUDA(cudaGetDevice(&dev));
     SF_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SF_TRY((mr_work_attr<KER, BW, CLIP, CNT, TZ>(&per_sm)));
-    b.slots = (int64_t)sms * per_sm;
+    b.slots = (int64_t)sms * per_sm;  // resident blocks of 8 persistent warps
+    const int64_t warps = b.slots * (kGridThreads / 32);
     const int64_t ips = std::max(1, items_per_slot);
-    uint32_t lpw = (uint32_t)std::max<int64_t>(16, (total + ips * b.slots - 1) / (ips * b.slots));
-    b.lpw = (lpw + 3) & ~3u;
+    uint32_t lpw = (uint32_t)std::max<int64_t>(8, (total + ips * warps - 1) / (ips * warps));
+    b.lpw = lpw;
     const int64_t max_items = a.ntiles + total / b.lpw + 1;
     auto get = [&](size_t bytes) -> void * {
         void *p = nullptr;
@@ -906,7 +1087,7 @@ static sf_status mr_plan(const MrArgs &a, uint32_t total, int items_per_slot, Mr
     b.ic = (uint32_t *)get(sizeof(uint32_t) * a.ntiles);
     b.ioff = (uint32_t *)get(sizeof(uint32_t) * a.ntiles);
     b.items = (int4 *)get(sizeof(int4) * max_items);
-    b.part = (double *)get(sizeof(double) * max_items * kGridThreads * TZ);
+    b.part = (double *)get(sizeof(double) * max_items * 32 * TZ);
     b.next = (unsigned int *)get(sizeof(unsigned int));
     if (!b.list || !b.ic || !b.ioff || !b.items || !b.part || !b.next)
         return fail(SF_ERR_OOM, "grid work buffers (%lld items)", (long long)max_items);
@@ -976,14 +1157,15 @@ static void node_axes(const GridSpec &g, float2 *ax) {
 }
 
 static RoiDesc roi_desc(const GridSpec &g, int tz, const float2 *axis, int tile_base, float *out,
-                        double *mass_part, const DensityParams *dp, const sf_box &roi) {
+                        double *mass_part, const DensityParams *dp, const sf_box &roi,
+                        int wx = kTileX, int wy = kTileY) {
     RoiDesc r;
     r.axis = axis;
     r.nx = g.nx;
     r.ny = g.ny;
     r.nz = g.nz;
-    r.tiles_x = (g.nx + kTileX - 1) / kTileX;
-    r.tiles_y = (g.ny + kTileY - 1) / kTileY;
+    r.tiles_x = (g.nx + wx - 1) / wx;
+    r.tiles_y = (g.ny + wy - 1) / wy;
     r.tiles_z = (g.nz + tz - 1) / tz;
     r.tile_base = tile_base;
     r.out = out;
@@ -999,7 +1181,7 @@ sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
     constexpr int TZ = kTileZ;
     std::vector<float2> ax((size_t)g.nx + g.ny + g.nz);
     node_axes(g, ax.data());
-    const int64_t tiles = (int64_t)((g.nx + kTileX - 1) / kTileX) * ((g.ny + kTileY - 1) / kTileY) *
+    const int64_t tiles = (int64_t)((g.nx + kWX - 1) / kWX) * ((g.ny + kWY - 1) / kWY) *
                           ((g.nz + TZ - 1) / TZ);
     if (tiles >= (int64_t(1) << 30)) return fail(SF_ERR_INVALID_ARG, "grid too large");
     Scratch sc(s);
@@ -1010,7 +1192,7 @@ sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
     SF_TRY_SCRATCH(sc);
     SF_TRY_CUDA(cudaMemcpyAsync(d_axis, ax.data(), ax.size() * sizeof(float2),
                                 cudaMemcpyHostToDevice, s));
-    const RoiDesc r = roi_desc(g, TZ, d_axis, 0, d_out, mass_part, call.dp, roi);
+    const RoiDesc r = roi_desc(g, TZ, d_axis, 0, d_out, mass_part, call.dp, roi, kWX, kWY);
     SF_TRY_CUDA(cudaMemcpyAsync(d_roi, &r, sizeof r, cudaMemcpyHostToDevice, s));
     SF_TRY_CUDA(cudaMemsetAsync(tile_roi, 0, sizeof(int) * tiles, s));
     MrArgs a;
@@ -1169,7 +1351,7 @@ sf_status batch_create(sf_index *idx, int nroi, const sf_box *rois, const GridSp
     for (int r = 0; r < nroi; ++r) {
         naxis += grids[r].nx + grids[r].ny + grids[r].nz;
         tb[r] = ntiles;
-        ntiles += (int64_t)((grids[r].nx + kTileX - 1) / kTileX) * ((grids[r].ny + kTileY - 1) / kTileY) *
+        ntiles += (int64_t)((grids[r].nx + kWX - 1) / kWX) * ((grids[r].ny + kWY - 1) / kWY) *
                   ((grids[r].nz + P->tz - 1) / P->tz);
     }
     if (ntiles >= (int64_t(1) << 30)) return bail(fail(SF_ERR_INVALID_ARG, "batch too large"));
@@ -1201,7 +1383,7 @@ sf_status batch_create(sf_index *idx, int nroi, const sf_box *rois, const GridSp
     for (int r = 0; r < nroi; ++r) {
         node_axes(grids[r], ax.data() + ao);
         P->h_rois[r] = roi_desc(grids[r], P->tz, d_axis + ao, (int)tb[r], nullptr, d_mp + tb[r],
-                                d_dps + r, rois[r]);
+                                d_dps + r, rois[r], kWX, kWY);
         const int64_t nt = (r + 1 < nroi ? tb[r + 1] : ntiles) - tb[r];
         for (int64_t t = 0; t < nt; ++t) tile_roi[tb[r] + t] = r;
         ao += grids[r].nx + grids[r].ny + grids[r].nz;
