@@ -39,6 +39,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Reciprocal of the hardware approximation (relative error below 2^-22). Used
+// for the conservative support filters and for u_k = s / l_k and c / prod l_k,
+// where a few ulps stay far inside the 1e-5 density tolerance.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Squared-support slack of the filters (covers the reciprocal's error and the
+// rounding of the gap terms; the filters only ever admit too much).
+constexpr float kFilterSlack = 3.0e-5f;
+
 // Kernel-specific constants, in the units of q' used on the device:
 //   EPAN : q' = sum (d_k / l_k)^2,           support q' < 1,  weight c (1 - q')
 //   GAUSS: q' = sum (d_k / l_k)^2 log2(e)/2, support q' < 9 log2(e)/2, weight c 2^-q'
@@ -703,6 +716,7 @@ __global__ void __launch_bounds__(kGridThreads)
         const RoiDesc &r = S.roi;
         // ---- the tile's node coordinates
         TileGeom g;
+        float isp[3], mlo[3], mhi[3];  // 1 / node spacing; tile box widened by the rounding margin
         tile_origin<TZ, kWX, kWY>(r, it.x - r.tile_base, g.gx0, g.gy0, g.gz0, g.nv);
         if (lane < kWX + kWY + TZ) {
             float2 v = make_float2(0.f, 0.f);
@@ -730,6 +744,10 @@ __global__ void __launch_bounds__(kGridThreads)
                 g.tlo[k] = S.axt[off[k]].x;
                 g.thi[k] = S.axt[off[k] + g.nv[k] - 1].x;
                 g.sp3[k] = g.nv[k] > 1 ? (S.axt[off[k] + 1].x - S.axt[off[k]].x) : 1.f;
+                isp[k] = g.sp3[k] > 0.f ? 1.0f / g.sp3[k] : 0.f;
+                const float mg = 1.0e-6f * (fabsf(g.tlo[k]) + fabsf(g.thi[k]));
+                mlo[k] = g.tlo[k] - mg;
+                mhi[k] = g.thi[k] + mg;
             }
         }
         float acc[TZ], sum[TZ], cmp[TZ];
@@ -741,7 +759,7 @@ __global__ void __launch_bounds__(kGridThreads)
             const int64_t i = (int64_t)list[lb] * kLeaf + lane;
             bool acc_pt = false;
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-            float l[3] = {0.f, 0.f, 0.f};
+            float l[3] = {0.f, 0.f, 0.f}, rl[3] = {0.f, 0.f, 0.f};
             int2 fp = make_int2(0, 0);
             if (i < E.tv.n) {
                 p = __ldg(&E.tv.pos[i]);
@@ -755,10 +773,11 @@ __global__ void __launch_bounds__(kGridThreads)
                 float qlb = 0.f;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
+                    rl[k] = BW == BW_ISO && k > 0 ? rl[0] : rcp_approx(l[k]);
                     const float R = l[k] * KDef<KER>::rmul;
                     if (g.sp3[k] > 0.f) {
-                        const float a0 = fminf(fmaxf(ceilf((pc[k] - R - g.tlo[k]) / g.sp3[k]) - 1.f, -1.f), 64.f);
-                        const float a1 = fminf(fmaxf(floorf((pc[k] + R - g.tlo[k]) / g.sp3[k]) + 1.f, -1.f), 64.f);
+                        const float a0 = fminf(fmaxf(ceilf((pc[k] - R - g.tlo[k]) * isp[k]) - 1.f, -1.f), 64.f);
+                        const float a1 = fminf(fmaxf(floorf((pc[k] + R - g.tlo[k]) * isp[k]) + 1.f, -1.f), 64.f);
                         f0[k] = max(0, (int)a0);
                         f1[k] = min(g.nv[k] - 1, (int)a1);
                     } else {
@@ -766,12 +785,10 @@ __global__ void __launch_bounds__(kGridThreads)
                         f1[k] = g.nv[k] - 1;
                     }
                     if (f0[k] > f1[k]) acc_pt = false;
-                    float gap = fmaxf(fmaxf(g.tlo[k] - pc[k], pc[k] - g.thi[k]), 0.f);
-                    gap = fmaxf(gap - 1.0e-6f * (fabsf(g.tlo[k]) + fabsf(g.thi[k])), 0.f);
-                    const float t = gap / R;
-                    qlb += t * t;
+                    const float t = fmaxf(fmaxf(mlo[k] - pc[k], pc[k] - mhi[k]), 0.f) * rl[k];
+                    qlb = fmaf(t, t, qlb);
                 }
-                if (!(qlb < 1.0f + 1.0e-5f)) acc_pt = false;
+                if (!(qlb < KDef<KER>::rmul * KDef<KER>::rmul * (1.0f + kFilterSlack))) acc_pt = false;
                 if (acc_pt) {
                     fp.x = f0[0] | (f1[0] << 8) | (f0[1] << 16) | (f1[1] << 24);
                     fp.y = f0[2] | (f1[2] << 8);
@@ -782,9 +799,9 @@ __global__ void __launch_bounds__(kGridThreads)
             if (ns == 0) continue;  // warp-uniform
             if (acc_pt) {
                 const int s = __popc(bal & ((1u << lane) - 1u));
-                S.sp[s] = make_float4(p.x, p.y, p.z, E.cnorm / ((l[0] * l[1]) * l[2]));
-                S.su[s] = make_float4(KDef<KER>::uscale / l[0], KDef<KER>::uscale / l[1],
-                                      KDef<KER>::uscale / l[2], 0.f);
+                S.sp[s] = make_float4(p.x, p.y, p.z, E.cnorm * ((rl[0] * rl[1]) * rl[2]));
+                S.su[s] = make_float4(KDef<KER>::uscale * rl[0], KDef<KER>::uscale * rl[1],
+                                      KDef<KER>::uscale * rl[2], 0.f);
                 S.sf[s] = fp;
             }
             __syncwarp();
@@ -1459,6 +1476,7 @@ template <int KER, int BW, bool CLIP, bool CNT>
 __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
     __shared__ PtWarpSmem W[kPtWarps];
     __shared__ float s_uni[3];
+    __shared__ float s_runi[4];  // 1 / uniform l_k, and whether all l_k > 0
     __shared__ double s_inv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
@@ -1466,6 +1484,10 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
         s_uni[0] = dp.ell_uniform[0];
         s_uni[1] = dp.ell_uniform[1];
         s_uni[2] = dp.ell_uniform[2];
+        s_runi[0] = 1.0f / s_uni[0];
+        s_runi[1] = 1.0f / s_uni[1];
+        s_runi[2] = 1.0f / s_uni[2];
+        s_runi[3] = (s_uni[0] > 0.f && s_uni[1] > 0.f && s_uni[2] > 0.f) ? 1.f : 0.f;
         s_inv = dp.inv_neff;
     }
     __syncthreads();
@@ -1492,6 +1514,14 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
             thi[k] = fmaxf(thi[k], __shfl_xor_sync(0xffffffffu, thi[k], o));
         }
     auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, s_uni, node, tlo, thi); };
+    // the query box widened by the rounding margin of the per-point filter
+    float mlo[3], mhi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float mg = 1.0e-6f * (fabsf(tlo[k]) + fabsf(thi[k]));
+        mlo[k] = tlo[k] - mg;
+        mhi[k] = thi[k] + mg;
+    }
 
     float sum = 0.f, cmp = 0.f;
     unsigned long long npairs = 0;
@@ -1525,16 +1555,18 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
                 }
             }
             bool ok = false;
-            float l[3] = {0.f, 0.f, 0.f};
+            float r[3] = {0.f, 0.f, 0.f};  // 1 / l_k
             if (j < a.e.tv.n) {
                 if (BW == BW_ISO) {
-                    l[0] = l[1] = l[2] = p.w;
+                    ok = p.w > 0.f;
+                    r[0] = r[1] = r[2] = rcp_approx(p.w);
                 } else if (BW == BW_UNIFORM) {
-                    l[0] = s_uni[0]; l[1] = s_uni[1]; l[2] = s_uni[2];
+                    ok = s_runi[3] > 0.f;
+                    r[0] = s_runi[0]; r[1] = s_runi[1]; r[2] = s_runi[2];
                 } else {
-                    l[0] = pe.x; l[1] = pe.y; l[2] = pe.z;
+                    ok = pe.x > 0.f && pe.y > 0.f && pe.z > 0.f;
+                    r[0] = rcp_approx(pe.x); r[1] = rcp_approx(pe.y); r[2] = rcp_approx(pe.z);
                 }
-                ok = l[0] > 0.f && l[1] > 0.f && l[2] > 0.f;
                 if (CLIP)
                     ok = ok && p.x >= a.e.blo[0] && p.x <= a.e.bhi[0] && p.y >= a.e.blo[1] &&
                          p.y <= a.e.bhi[1] && p.z >= a.e.blo[2] && p.z <= a.e.bhi[2];
@@ -1542,22 +1574,20 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
                 float qlb = 0.f;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    float gap = fmaxf(fmaxf(tlo[k] - pc[k], pc[k] - thi[k]), 0.f);
-                    gap = fmaxf(gap - 1.0e-6f * (fabsf(tlo[k]) + fabsf(thi[k])), 0.f);
-                    const float t = gap / (l[k] * KDef<KER>::rmul);
-                    qlb += t * t;
+                    const float t = fmaxf(fmaxf(mlo[k] - pc[k], pc[k] - mhi[k]), 0.f) * r[k];
+                    qlb = fmaf(t, t, qlb);
                 }
-                ok = ok && qlb < 1.0f + 1.0e-5f;
+                ok = ok && qlb < KDef<KER>::rmul * KDef<KER>::rmul * (1.0f + kFilterSlack);
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             if (ok) {
                 const int s = __popc(m & ((1u << lane) - 1u));
-                S.sp[s] = make_float4(p.x, p.y, p.z, a.e.cnorm / ((l[0] * l[1]) * l[2]));
-                const float u0 = KDef<KER>::uscale / l[0];
+                S.sp[s] = make_float4(p.x, p.y, p.z, a.e.cnorm * ((r[0] * r[1]) * r[2]));
+                const float u0 = KDef<KER>::uscale * r[0];
                 if (BW == BW_ISO) {
                     S.su[s] = make_float4(u0 * u0, 0.f, 0.f, 0.f);
                 } else {
-                    S.su[s] = make_float4(u0, KDef<KER>::uscale / l[1], KDef<KER>::uscale / l[2], 0.f);
+                    S.su[s] = make_float4(u0, KDef<KER>::uscale * r[1], KDef<KER>::uscale * r[2], 0.f);
                 }
             }
             __syncwarp();
