@@ -48,6 +48,36 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// Packed FP32 pairs (two IEEE single-precision lanes per 64-bit register,
+// one instruction for both; each lane rounds exactly like the scalar op).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_ld(const float *p) {  // 8-byte aligned
+    return *reinterpret_cast<const f32x2 *>(p);
+}
+
 // Squared-support slack of the filters (covers the reciprocal's error and the
 // rounding of the gap terms; the filters only ever admit too much).
 constexpr float kFilterSlack = 3.0e-5f;
@@ -1465,11 +1495,14 @@ struct PointsArgs {
     unsigned long long *pairs;  // counting variant
 };
 
-struct PtWarpSmem {
+constexpr int kPtRing = 2 * kLeaf;  // staged candidates: two halves of 32
+
+struct __align__(16) PtWarpSmem {
+    // staged candidates as structure of arrays (pairs of entries load as one 64-bit word)
+    float sx[kPtRing], sy[kPtRing], sz[kPtRing], sc[kPtRing];
+    float su[3][kPtRing];  // BW_ISO: su[0] = u^2; else u_x, u_y, u_z
     int stack[kStack];
     int leaves[kBatch];
-    float4 sp[kLeaf];
-    float4 su[kLeaf];
 };
 
 template <int KER, int BW, bool CLIP, bool CNT>
@@ -1525,6 +1558,42 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
 
     float sum = 0.f, cmp = 0.f;
     unsigned long long npairs = 0;
+    const f32x2 QX = f2_pack(q.x, q.x), QY = f2_pack(q.y, q.y), QZ = f2_pack(q.z, q.z);
+    // entries s and s + 1 (s even) against this lane's query
+    auto pair2 = [&](int s, f32x2 &acc) {
+        const f32x2 dx = f2_sub(QX, f2_ld(&S.sx[s]));
+        const f32x2 dy = f2_sub(QY, f2_ld(&S.sy[s]));
+        const f32x2 dz = f2_sub(QZ, f2_ld(&S.sz[s]));
+        f32x2 qq;
+        if (BW == BW_ISO) {
+            qq = f2_mul(f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx))), f2_ld(&S.su[0][s]));
+        } else {
+            const f32x2 tx = f2_mul(dx, f2_ld(&S.su[0][s]));
+            const f32x2 ty = f2_mul(dy, f2_ld(&S.su[1][s]));
+            const f32x2 tz = f2_mul(dz, f2_ld(&S.su[2][s]));
+            qq = f2_fma(tz, tz, f2_fma(ty, ty, f2_mul(tx, tx)));
+        }
+        float q0, q1;
+        f2_unpack(qq, q0, q1);
+        const bool in0 = q0 < KDef<KER>::qmax, in1 = q1 < KDef<KER>::qmax;
+        float w0, w1;
+        if (KER == SF_K_GAUSS3) {
+            w0 = in0 ? ex2_approx(-q0) : 0.f;
+            w1 = in1 ? ex2_approx(-q1) : 0.f;
+        } else {
+            w0 = in0 ? 1.0f - q0 : 0.f;
+            w1 = in1 ? 1.0f - q1 : 0.f;
+        }
+        acc = f2_fma(f2_ld(&S.sc[s]), f2_pack(w0, w1), acc);
+        if (CNT) npairs += (unsigned)in0 + (unsigned)in1;
+    };
+    auto add = [&](float v) {  // compensated running sum (TwoSum)
+        const float t = sum + v;
+        const float bp = t - sum;
+        cmp += (sum - (t - bp)) + (v - bp);
+        sum = t;
+    };
+    int head = 0, cnt = 0;  // ring of staged candidates: first entry, count (warp-uniform)
     int spv;
     int nl = warp_walk_start(a.e.tv, test, S.stack, spv, S.leaves);
     while (true) {
@@ -1581,52 +1650,54 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             if (ok) {
-                const int s = __popc(m & ((1u << lane) - 1u));
-                S.sp[s] = make_float4(p.x, p.y, p.z, a.e.cnorm * ((r[0] * r[1]) * r[2]));
+                const int s = (head + cnt + __popc(m & ((1u << lane) - 1u))) & (kPtRing - 1);
+                S.sx[s] = p.x;
+                S.sy[s] = p.y;
+                S.sz[s] = p.z;
+                S.sc[s] = a.e.cnorm * ((r[0] * r[1]) * r[2]);
                 const float u0 = KDef<KER>::uscale * r[0];
                 if (BW == BW_ISO) {
-                    S.su[s] = make_float4(u0 * u0, 0.f, 0.f, 0.f);
+                    S.su[0][s] = u0 * u0;
                 } else {
-                    S.su[s] = make_float4(u0, KDef<KER>::uscale * r[1], KDef<KER>::uscale * r[2], 0.f);
+                    S.su[0][s] = u0;
+                    S.su[1][s] = KDef<KER>::uscale * r[1];
+                    S.su[2][s] = KDef<KER>::uscale * r[2];
                 }
             }
-            __syncwarp();
-            const int ns = __popc(m);
-            float acc0 = 0.f, acc1 = 0.f;
-            auto pair = [&](int s, float &acc) {
-                const float4 P = S.sp[s];
-                float qq;
-                if (BW == BW_ISO) {
-                    const float u2 = S.su[s].x;
-                    const float dx = q.x - P.x, dy = q.y - P.y, dz = q.z - P.z;
-                    qq = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) * u2;
-                } else {
-                    const float4 U = S.su[s];
-                    const float tx = (q.x - P.x) * U.x;
-                    const float ty = (q.y - P.y) * U.y;
-                    const float tz = (q.z - P.z) * U.z;
-                    qq = fmaf(tz, tz, fmaf(ty, ty, tx * tx));
-                }
-                if (qq < KDef<KER>::qmax) {
-                    if (KER == SF_K_GAUSS3) acc = fmaf(P.w, ex2_approx(-qq), acc);
-                    else acc = fmaf(P.w, 1.0f - qq, acc);
-                    if (CNT) ++npairs;
-                }
-            };
-            int s = 0;
-            for (; s + 2 <= ns; s += 2) {
-                pair(s, acc0);
-                pair(s + 1, acc1);
+            cnt += __popc(m);
+            if (cnt >= kLeaf) {  // warp-uniform: a full half of the ring is staged
+                __syncwarp();
+                f32x2 acc[2] = {0ull, 0ull};
+#pragma unroll
+                for (int e = 0; e < kLeaf; e += 2) pair2(head + e, acc[(e >> 1) & 1]);
+                head ^= kLeaf;
+                cnt -= kLeaf;
+                float a0, a1, a2, a3;
+                f2_unpack(acc[0], a0, a1);
+                f2_unpack(acc[1], a2, a3);
+                add((a0 + a1) + (a2 + a3));
+                __syncwarp();
             }
-            if (s < ns) pair(s, acc0);
-            __syncwarp();
-            const float acc = acc0 + acc1;
-            const float t = sum + acc;
-            const float bp = t - sum;
-            cmp += (sum - (t - bp)) + (acc - bp);
-            sum = t;
         }
         nl = 0;
+    }
+    // the staged remainder (cnt < 32 entries from head), padded to an even
+    // count with an entry of zero weight
+    if (cnt & 1) {
+        if (lane == 0) {
+            const int s = (head + cnt) & (kPtRing - 1);
+            S.sx[s] = S.sy[s] = S.sz[s] = S.sc[s] = 0.f;
+            S.su[0][s] = S.su[1][s] = S.su[2][s] = 0.f;
+        }
+    }
+    __syncwarp();
+    if (cnt > 0) {
+        f32x2 acc = 0ull;
+        for (int e = 0; e < cnt; e += 2) pair2(head + e, acc);
+        if (CNT && (cnt & 1)) --npairs;  // the padding entry is "in support" (q = 0)
+        float a0, a1;
+        f2_unpack(acc, a0, a1);
+        add(a0 + a1);
     }
     if (active) a.rho_sorted[qi] = (float)(((double)sum + (double)cmp) * s_inv);
     if (CNT) {
