@@ -8,7 +8,7 @@
 // Persistent warps; each takes the next leaf of 32 Morton-consecutive query
 // points from an atomic counter (no warp waits for another):
 //  1. radius bound: per lane, the k-th smallest FP32 d2 among the points of
-//     the next leaves in sorted order, bracketed by three rounds of 32-bin
+//     the next leaves in sorted order, bracketed by two rounds of 32-bin
 //     histograms -- an upper bound of the true k-th distance;
 //  2. candidates: the index walk keeps the leaves within that radius of at
 //     least one lane's point; their points inside the warp's envelope box are
@@ -30,7 +30,7 @@ namespace sf {
 
 constexpr int kKnnWarps = 4;
 constexpr int kNB = 32;        // histogram bins per lane
-constexpr int kBand = 16;      // band buffer per lane
+constexpr int kBand = 4;       // band buffer per lane (small: shared memory sets the occupancy)
 constexpr int kCand = 64;      // candidate leaves per walk batch
 constexpr int kCache = 32768;  // candidate points per warp buffer (global)
 constexpr int kKStack = 32 * kMaxLevels;
@@ -291,7 +291,7 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
         }
     };
     float wlo = 0.f;
-    for (int round = 0; round < 3; ++round) {
+    for (int round = 0; round < 2; ++round) {  // two rounds: the bound is then within 0.1% of the window k-th
         clear_hist();
         const float width = whi - wlo;
         const float inv = width > 0.f ? (float)kNB / width : 0.f;
