@@ -10,6 +10,9 @@ as plain definitions in double precision over all pairs:
 
 * ``grid_nodes``      uniform grid of nodes over the closed box B (Sec. 3.1)
 * ``knn``             k-nearest-neighbour bandwidth h_j (kNN rule; brute force)
+* ``knn_tree``        the same for every point of a large cloud, through a plain
+                      binary k-d tree that only skips subtrees beyond the k-th
+                      distance (pinned against ``knn`` bit for bit)
 * ``density_at``      rho(r) = (1/N) sum_j K(r - y_j; l_j)        (Eqs. 2, 4, 7)
 * ``kde_grid``        rho at every node, x fastest (Algorithm 4 layout)
 * ``percentile_linear`` P_k^(q) of Eq. 1
@@ -65,6 +68,8 @@ def _load():
                                       ctypes.POINTER(ctypes.c_uint8))
         lib.or_knn.argtypes = [f32p, i64, ctypes.c_int, i64p, i64, f32p, i64p, f64p]
         lib.or_knn.restype = ctypes.c_int
+        lib.or_knn_tree.argtypes = [f32p, i64, ctypes.c_int, f32p, i64p]
+        lib.or_knn_tree.restype = ctypes.c_int
         lib.or_density_at.argtypes = [f32p, i64, f64p, u8p, ctypes.c_double, ctypes.c_int,
                                       ctypes.c_double, f64p, i64, f64p, f64p, f64p, i64p,
                                       ctypes.c_double]
@@ -123,6 +128,25 @@ def knn(xyz, k: int, queries=None, want_neighbours: bool = False):
     if rc != 0:
         raise ValueError("or_knn failed")
     return h, nbr, d2
+
+
+def knn_tree(xyz, k: int, want_neighbours: bool = False):
+    """k nearest neighbours of every point (same definition as ``knn``) through a
+    binary k-d tree: for clouds where the all-pairs loop is out of reach.
+
+    Returns (h float32 [n], nbr int64 [n, k] or None).
+    """
+    a = _xyz(xyz)
+    n = a.shape[0]
+    if k < 1 or n <= k:
+        raise ValueError("need 1 <= k < N")
+    h = np.empty(n, dtype=np.float32)
+    nbr = np.empty((n, k), dtype=np.int64) if want_neighbours else None
+    rc = _load().or_knn_tree(_ptr(a, ctypes.c_float), n, int(k), _ptr(h, ctypes.c_float),
+                             _ptr(nbr, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError("or_knn_tree failed")
+    return h, nbr
 
 
 # ---------------------------------------------------------------------------

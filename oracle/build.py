@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "sf_oracle.c")
+SRCS = [os.path.join(HERE, "sf_oracle.c"), os.path.join(HERE, "sf_oracle_kdtree.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
@@ -16,14 +16,14 @@ LIB = os.path.join(OUT_DIR, "liboracle.so")
 def build(force: bool = False) -> str:
     """Build liboracle.so if missing or older than its source; return its path."""
     if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+            and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in SRCS)):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + f".tmp{os.getpid()}"
     # -ffp-contract=off: no fused multiply-add, every double op rounds once.
     # No -ffast-math and no -march flags, so x86 and Arm hosts agree.
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", SRC, "-o", tmp, "-lm"]
+           "-ffp-contract=off", *SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

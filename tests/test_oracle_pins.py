@@ -186,6 +186,29 @@ def test_knn_rejects_degenerate():
         oracle.knn(np.zeros((4, 3), np.float32), 4)
 
 
+@pytest.mark.parametrize("k", [1, 8, 33, 64])
+def test_knn_tree_matches_brute_force(k):
+    """The k-d tree route (used at sizes brute force cannot reach) gives the brute-force
+    bandwidths and neighbour lists bit for bit: clustered cloud, duplicates, lattice ties."""
+    parts = [synth.cosmology_cloud(6000, seed=21, levels=7), synth.plain_cloud(3000, seed=22),
+             synth.lattice_cloud(6, 0.0625, origin=0.3)]
+    dup = parts[0][:200].copy()
+    xyz = np.ascontiguousarray(np.concatenate(parts + [dup]))
+    h, nbr = oracle.knn_tree(xyz, k, want_neighbours=True)
+    h0, nbr0, _ = oracle.knn(xyz, k, want_neighbours=True)
+    assert np.array_equal(h.view(np.uint32), h0.view(np.uint32))
+    assert np.array_equal(nbr, nbr0)
+
+
+def test_knn_tree_small_and_degenerate():
+    xyz = synth.uniform_cloud(17, seed=4)
+    h, nbr = oracle.knn_tree(xyz, 16, want_neighbours=True)
+    h0, nbr0, _ = oracle.knn(xyz, 16, want_neighbours=True)
+    assert np.array_equal(h, h0) and np.array_equal(nbr, nbr0)
+    with pytest.raises(ValueError):
+        oracle.knn_tree(np.zeros((4, 3), np.float32), 4)
+
+
 # --------------------------------------------------------------------------
 # Modified Breiman estimator pieces
 # --------------------------------------------------------------------------
