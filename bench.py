@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="cloud size (smaller clouds are for profiling only, not bench lines)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop sample")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-vs-plain comparison over 64 uneven ROIs")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--no-count", action="store_true",
                     help="skip the pair-counting pass (value and roofline become null)")
@@ -350,6 +352,11 @@ def main():
     if not args.no_serve:
         serving = run_serving(args, L, torch, d_xyz, p, rois)
 
+    # ---- 64 uneven ROIs: one graph-captured persistent execution vs 64 plain calls
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(args, L, torch, d_xyz, p, stream)
+
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -373,6 +380,7 @@ def main():
                 "kernels_ms_per_step": {k: v["ms_total"] / args.steps for k, v in kern.items()},
                 "kernels_ms_per_roi": {k: v.get("per_roi_ms") for k, v in kern.items() if "per_roi_ms" in v},
                 "serving": serving,
+                "batched": batched,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -433,7 +441,8 @@ def run_serving(args, L, torch, d_xyz, p, rois):
     try:
         L.sf_bandwidths(idx, p)
         centre = [(float(rois[-1][0][k]) + float(rois[-1][1][k])) / 2 for k in range(3)]
-        reqs = serve.navigation_requests(args.serve_requests, rate=200.0, centre=centre, seed=2601)
+        reqs = serve.navigation_requests(args.serve_requests, rate=200.0, centre=centre, seed=2601,
+                                         select_every=10)
         free, _ = torch.cuda.mem_get_info()
         slots = 4
         ex = serve.GpuExecutor(idx, p, L.SF_K_GAUSS3, n, slots=slots, max_nodes=256 ** 3)
@@ -448,11 +457,83 @@ def run_serving(args, L, torch, d_xyz, p, rois):
             srv.close()
         st["rate_per_s"] = 200.0
         st["stream"] = ("Poisson arrivals, zoom walk over log10 edge in [-3, 0] (sigma 0.1 decade), "
-                        "pan <= half an edge, grid edge in {64, 96, 128, 192, 256}^3, "
-                        "grid + point densities + 90th-percentile selection per request")
+                        "pan <= half an edge, grid edge in {64, 96, 128, 192, 256}^3; every request "
+                        "recomputes the ROI grid, every 10th also the ROI point densities and the "
+                        "90th-percentile selection")
         return st
     finally:
         L.sf_free_index(idx)
+
+
+def batch_rois(torch, d_xyz, n_roi=64, seed=4):
+    """Uneven cubic ROIs over the cloud: centres at seeded cloud points, half-edges
+    set to the Chebyshev distance that holds a log-uniform target count in
+    [1e4, N/2] around the centre (clipped to the unit cube), grid edges
+    log-uniform in [32, 256] nodes."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    n = d_xyz.shape[0]
+    centres = rng.choice(n, n_roi, replace=False)
+    targets = np.exp(rng.uniform(np.log(1e4), np.log(n / 2), n_roi)).astype(np.int64)
+    edges = np.rint(np.exp(rng.uniform(np.log(32), np.log(256), n_roi))).astype(int)
+    boxes, dims = [], []
+    for c, t, g in zip(centres, targets, edges):
+        cc = d_xyz[int(c)].double()
+        cheb = (d_xyz.double() - cc).abs().amax(dim=1)
+        half = float(torch.kthvalue(cheb, int(t)).values)
+        lo = [max(0.0, float(cc[k]) - half) for k in range(3)]
+        hi = [min(1.0, float(cc[k]) + half) for k in range(3)]
+        boxes.append((lo, hi))
+        dims.append((int(g), int(g), int(g)))
+    return boxes, dims, targets
+
+
+def run_batched(args, L, torch, d_xyz, p, stream):
+    """The same 64 uneven ROI grids computed as 64 sf_kde_grid calls and as one
+    autotuned, graph-captured batch; both timed with CUDA events on one stream."""
+    from paper_2601_20758_gb300 import autotune
+    rois, dims, targets = batch_rois(torch, d_xyz)
+    boxes = [L.make_box(lo, hi) for lo, hi in rois]
+    idx = L.sf_build_index(d_xyz, stream)
+    try:
+        L.sf_bandwidths(idx, p, stream)
+        outs_p = [torch.empty(d[0] * d[1] * d[2], device="cuda") for d in dims]
+        outs_b = [torch.empty_like(o) for o in outs_p]
+        tz, ips, tms = autotune.tune_batch(idx, boxes, dims, L.SF_K_GAUSS3, p, outs_b, stream)
+        plan = L.sf_batch_create(idx, boxes, dims, L.SF_K_GAUSS3, p, autotune.make_tune(tz, ips), stream)
+        try:
+            def plain():
+                for b, d, o in zip(boxes, dims, outs_p):
+                    L.sf_kde_grid(idx, b, d, L.SF_K_GAUSS3, p, o, stream=stream)
+
+            def batch():
+                L.sf_batch_run(plan, outs_b, stream=stream)
+
+            res = {}
+            for name, fn in (("plain", plain), ("batched", batch)):
+                fn()
+                torch.cuda.synchronize()
+                ms = []
+                for _ in range(3):
+                    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn()
+                    z.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(a.elapsed_time(z))
+                res[name] = sorted(ms)[1]
+            diff = max(float(((x - y).abs().max() / y.abs().max().clamp_min(1e-30)))
+                       for x, y in zip(outs_b, outs_p))
+        finally:
+            L.sf_batch_free(plan)
+    finally:
+        L.sf_free_index(idx)
+    return {"rois": len(boxes), "nodes": int(sum(d[0] * d[1] * d[2] for d in dims)),
+            "inside_target": [int(targets.min()), int(targets.max())],
+            "grid_edges": [int(min(d[0] for d in dims)), int(max(d[0] for d in dims))],
+            "plain_ms": res["plain"], "batched_ms": res["batched"],
+            "speedup": res["plain"] / res["batched"], "tile_z": tz, "items_per_warp": ips,
+            "tuning_ms": tms, "max_rel_diff_vs_plain": diff}
 
 
 def run_e2e(args, L, torch, xyz, boxes, p, pairs_step, stream, world, barrier, dist):

@@ -221,9 +221,10 @@ sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids
 /*
  * Batched ROI grids: many ROIs of uneven size in one persistent execution.
  *
- * Every (ROI, 16x16xZ node tile) lists its candidate leaves, the lists are cut
- * into work items of similar size, one persistent kernel drains the items of
- * all ROIs, and each tile adds its items' partial sums in a fixed order: a
+ * Every (ROI, 8x4xZ node tile) lists its candidate leaves, the lists are cut
+ * into work items of similar size, one persistent kernel (one warp per item at
+ * a time) drains the items of all ROIs, and each tile adds its items' partial
+ * sums in a fixed order: a
  * plan's results are bit-identical from run to run, and equal sf_kde_grid's up
  * to the final rounding to float (the items are cut differently). sf_batch_create sizes the buffers (it synchronises the stream)
  * and, unless tune->no_graph, captures the execution into a CUDA graph that
@@ -238,7 +239,7 @@ sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids
 typedef struct sf_batch sf_batch;
 typedef struct {
     int32_t tile_z;          /* node tile depth in z: 4 or 8 (0: 8)                 */
-    int32_t items_per_slot;  /* work items per resident CTA, 1..64 (0: 4)           */
+    int32_t items_per_slot;  /* work items per resident warp, 1..64 (0: 4)          */
     int32_t no_graph;        /* 1: launch the kernels directly instead of a graph   */
     int32_t reserved;        /* must be 0                                           */
 } sf_tune;

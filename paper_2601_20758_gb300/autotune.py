@@ -1,8 +1,8 @@
 """Autotuner for batched ROI grids (sf_batch_create's sf_tune knobs).
 
-The knobs are the node tile depth in z (4 or 8: a 16 x 16 x 4 or 16 x 16 x 8
-tile per CTA) and the number of work items per resident CTA (the granularity
-at which dense tiles are split). For a given index and batch shape, every
+The knobs are the node tile depth in z (4 or 8: an 8 x 4 x 4 or 8 x 4 x 8
+tile per warp) and the number of work items per resident warp (the
+granularity at which dense tiles are split). For a given index and batch shape, every
 candidate is planned, warmed up and timed with CUDA events on the caller's
 stream; the fastest is cached in a JSON file keyed by the batch's signature
 (points, ROI count, total nodes, kernel, rule, scope), so later plans of the

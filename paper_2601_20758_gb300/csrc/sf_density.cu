@@ -7,17 +7,24 @@
 // output is written by exactly one thread, in a fixed summation order: no
 // atomics, results are deterministic.
 //
-// Grid: one CTA per 16 x 16 x 8 voxel tile; each thread owns one (x, y) column
-// of 8 voxels in registers. Warp 0 walks the index for leaves whose support
-// reaches the tile; their points are refined (footprint in the tile, ROI
-// clip) and staged in shared memory, together with per-axis tables of the
-// kernel factors at the tile's node coordinates, so the inner loop per
-// (point, voxel) pair is two instructions (Gaussian: exp(a+b+c) = e^a e^b e^c
-// with the truncation test on q_x + q_y < 9 - q_z) or three (Epanechnikov).
+// Grid, split pipeline (sf_kde_grid, batches): the ROI's nodes are cut into
+// 8 x 4 x Z tiles, one warp each. A walk kernel lists every tile's candidate
+// leaves (leaves whose support reaches the tile); the lists are cut into work
+// items of similar length; persistent warps drain the items, each lane owning
+// one (x, y) column of Z nodes in registers. Per candidate leaf the warp
+// refines its points (footprint in the tile, ROI clip), stages them in its own
+// shared memory with per-axis tables of the kernel factors at the tile's node
+// coordinates, so the inner loop per (point, node) pair is two instructions
+// (Gaussian: exp(a+b+c) = e^a e^b e^c with the truncation test on
+// q_x + q_y < 9 - q_z) or three (Epanechnikov). A last kernel adds each tile's
+// item partials in item order (deterministic). The allocation-free entry point
+// keeps the older monolithic form: one CTA per 16 x 16 x 8 tile walking and
+// summing in one launch.
 //
 // Points: one warp per leaf of 32 query points; the warp walks the index for
 // leaves whose support reaches the query points' box, stages the candidates
-// in shared memory and every lane sums over them for its own point.
+// in a shared-memory ring and every lane sums over them for its own point,
+// two candidates per instruction (packed FP32x2 arithmetic).
 #include <cmath>
 #include <vector>
 

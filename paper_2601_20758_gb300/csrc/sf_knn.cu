@@ -220,10 +220,14 @@ struct KnnWarp {
     __device__ void each(Fn fn) {
         const int lane = threadIdx.x & 31;
         if (!overflow) {
+            // the next chunk is loaded while the current one is processed
+            float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (lane < ncache) nxt = cache[lane];
             for (int base = 0; base < ncache; base += 32) {
                 const int n = min(32, ncache - base);
-                if (lane < n) S.pts[lane] = cache[base + lane];
+                if (lane < n) S.pts[lane] = nxt;
                 __syncwarp();
+                if (base + 32 + lane < ncache) nxt = cache[base + 32 + lane];
                 int t = 0;
                 for (; t + 2 <= n; t += 2) {
                     const float4 a = S.pts[t], b = S.pts[t + 1];
@@ -490,7 +494,7 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
     }
 }
 
-__global__ void __launch_bounds__(kKnnWarps * 32) k_knn(KnnArgs a) {
+__global__ void __launch_bounds__(kKnnWarps * 32, 6) k_knn(KnnArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
     KnnWarpSmem &S = reinterpret_cast<KnnWarpSmem *>(smem_raw)[warp];

@@ -212,11 +212,13 @@ class GpuExecutor:
 
 
 def navigation_requests(n: int, rate: float, centre, seed: int, edges=(64, 96, 128, 192, 256),
-                        log_range=(-3.0, 0.0), step_decades=0.1):
+                        log_range=(-3.0, 0.0), step_decades=0.1, select_every: int = 0):
     """Seeded progressive-navigation stream: Poisson arrivals at `rate` per second;
     the ROI scale walks in log10 space with Gaussian steps (reflected at the range
     ends), the centre pans by up to half an edge per step; grid edges uniform in
-    `edges`. Cubic ROIs kept inside the unit cube."""
+    `edges`. Cubic ROIs kept inside the unit cube. A view change recomputes the
+    ROI grid; with select_every = m > 0, every m-th request also recomputes the
+    ROI's point densities and the percentile selection."""
     rng = np.random.default_rng(seed)
     t = 0.0
     scale = log_range[1] - 0.5
@@ -235,5 +237,5 @@ def navigation_requests(n: int, rate: float, centre, seed: int, edges=(64, 96, 1
         c = np.clip(c, e / 2, 1 - e / 2)
         g = int(rng.choice(edges))
         out.append(Request(rid=i, lo=tuple(c - e / 2), hi=tuple(c + e / 2), dims=(g, g, g),
-                           arrival=t))
+                           arrival=t, want_points=bool(select_every) and i % select_every == 0))
     return out

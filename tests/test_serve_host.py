@@ -73,6 +73,10 @@ def test_navigation_stream_is_seeded_and_in_the_unit_cube():
         assert r.dims[0] in (64, 96, 128, 192, 256)
     gaps = [y.arrival - x.arrival for x, y in zip(a, a[1:])]
     assert sum(gaps) / len(gaps) == pytest.approx(1 / 200.0, rel=0.25)
+    assert not any(r.want_points for r in a)      # view changes recompute the grid only
+    c = serve.navigation_requests(200, rate=200.0, centre=(0.3, 0.4, 0.5), seed=5, select_every=10)
+    assert [r.want_points for r in c] == [i % 10 == 0 for i in range(200)]
+    assert [(r.lo, r.dims) for r in c] == [(r.lo, r.dims) for r in a]
 
 
 def test_percentile_nearest_rank():
