@@ -724,7 +724,7 @@ struct WTileSmem {
 // sums them into the item's partial grid. No block barriers: a warp owns its
 // tile, its staging and its tables.
 template <int KER, int BW, bool CLIP, bool CNT, int TZ>
-__global__ void __launch_bounds__(kGridThreads)
+__global__ void __launch_bounds__(kGridThreads, 4)
     k_mr_work(MrArgs a, const int4 *__restrict__ items, const uint32_t *__restrict__ n_items,
               const int *__restrict__ list, double *__restrict__ part, unsigned int *next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -842,7 +842,8 @@ __global__ void __launch_bounds__(kGridThreads)
                 S.sf[s] = fp;
             }
             __syncwarp();
-            // ---- per-axis tables, footprint entries only
+            // ---- per-axis tables over the whole tile: factors inside the footprint,
+            // "no support" values outside it (so the accumulation needs no range tests)
             constexpr int kEnt = kWX + kWY + TZ;
             for (int e = lane; e < ns * kEnt; e += 32) {
                 const int s = e / kEnt;
@@ -856,7 +857,7 @@ __global__ void __launch_bounds__(kGridThreads)
                 } else {
                     axis = 2; ii = j - kWX - kWY; lo_i = F.y & 255; hi_i = (F.y >> 8) & 255;
                 }
-                if (ii < lo_i || ii > hi_i) continue;
+                const bool inside = ii >= lo_i && ii <= hi_i;
                 const float4 P = S.sp[s];
                 const float4 U = S.su[s];
                 const float pc = axis == 0 ? P.x : (axis == 1 ? P.y : P.z);
@@ -865,7 +866,7 @@ __global__ void __launch_bounds__(kGridThreads)
                 const float d = (nc.x - pc) + nc.y;
                 const float t = d * u;
                 const float q = t * t;
-                const bool sup = q < KDef<KER>::qmax;
+                const bool sup = inside && q < KDef<KER>::qmax;
                 float2 v;
                 if (KER == SF_K_GAUSS3) {
                     const float w = sup ? ex2_approx(-q) : 0.f;
@@ -883,39 +884,26 @@ __global__ void __launch_bounds__(kGridThreads)
             __syncwarp();
             // ---- accumulate: lane owns column (cx, cy) and TZ nodes in z
             for (int s = 0; s < ns; ++s) {
-                const int2 F = S.sf[s];
-                const int x0 = F.x & 255, x1 = (F.x >> 8) & 255;
-                const int y0 = (F.x >> 16) & 255, y1 = (F.x >> 24) & 255;
-                const int z0 = F.y & 255, z1 = (F.y >> 8) & 255;
-                const bool in = cx >= x0 && cx <= x1 && cy >= y0 && cy <= y1;
-                float2 ex = KER == SF_K_GAUSS3 ? make_float2(0.f, kBig) : make_float2(kBig, 0.f);
-                float2 ey = ex;
-                if (in) {
-                    ex = S.tx[s][cx];
-                    ey = S.ty[s][cy];
-                }
+                const float2 ex = S.tx[s][cx];
+                const float2 ey = S.ty[s][cy];
                 if (KER == SF_K_GAUSS3) {
                     const float bse = ex.x * ey.x;
                     const float qij = ex.y + ey.y;
 #pragma unroll
                     for (int k = 0; k < TZ; ++k) {
-                        if (k >= z0 && k <= z1) {
-                            const float2 ez = S.tz[s][k];
-                            if (qij < ez.y) {
-                                acc[k] = fmaf(bse, ez.x, acc[k]);
-                                if (CNT) ++np;
-                            }
+                        const float2 ez = S.tz[s][k];
+                        if (qij < ez.y) {
+                            acc[k] = fmaf(bse, ez.x, acc[k]);
+                            if (CNT) ++np;
                         }
                     }
                 } else {
                     const float b = S.sp[s].w * (ex.x + ey.x);
 #pragma unroll
                     for (int k = 0; k < TZ; ++k) {
-                        if (k >= z0 && k <= z1) {
-                            const float t = S.tz[s][k].x - b;
-                            acc[k] += fmaxf(t, 0.f);
-                            if (CNT) np += (t > 0.f);
-                        }
+                        const float t = S.tz[s][k].x - b;
+                        acc[k] += fmaxf(t, 0.f);
+                        if (CNT) np += (t > 0.f);
                     }
                 }
             }
