@@ -263,7 +263,7 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
 
     // ---- 1. radius bound from the neighbouring leaves in sorted order
     const int64_t nleaf = tv.cnt[0];
-    const int64_t wl = (int64_t)((k + 1 + 31) / 32) + 2;
+    const int64_t wl = (int64_t)((k + 1 + 31) / 32) + 10;  // 13 leaves at k = 64 (a wider window gives a tighter bound)
     int64_t w0 = leaf - wl / 2, w1;
     if (w0 < 0) w0 = 0;
     w1 = w0 + wl - 1;
