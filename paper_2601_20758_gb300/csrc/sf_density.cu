@@ -116,11 +116,12 @@ struct EngineArgs {
     float blo[3], bhi[3];    // clip box, float bounds equivalent to the closed double box
 };
 
-// Does node i possibly hold a particle whose support reaches the box [tlo, thi]?
-// Conservative: gaps are shrunk by a margin covering float rounding of the box.
+// Does node i possibly hold a particle whose support reaches the box [wlo, whi]?
+// Conservative: the box comes widened by widen_box (a margin covering float
+// rounding of the box), and the squared-support test carries kFilterSlack.
 template <int KER, int BW, bool CLIP>
 __device__ __forceinline__ bool node_reaches(const EngineArgs &a, const float *uni, int64_t i,
-                                             const float tlo[3], const float thi[3]) {
+                                             const float wlo[3], const float whi[3]) {
     const float4 lo = __ldg(&a.tv.nlo[i]);
     const float4 hi = __ldg(&a.tv.nhi[i]);
     float e[3];
@@ -144,13 +145,23 @@ __device__ __forceinline__ bool node_reaches(const EngineArgs &a, const float *u
     float q = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float gap = fmaxf(fmaxf(nl[k] - thi[k], tlo[k] - nh[k]), 0.f);
-        float margin = 1.0e-6f * (fabsf(tlo[k]) + fabsf(thi[k])) + 1.0e-30f;
-        gap = fmaxf(gap - margin, 0.f);
-        float t = gap / (e[k] * KDef<KER>::rmul);
-        q += t * t;
+        const float gap = fmaxf(fmaxf(nl[k] - whi[k], wlo[k] - nh[k]), 0.f);
+        const float t = gap * rcp_approx(e[k]);
+        q = fmaf(t, t, q);
     }
-    return q < 1.0f + 1.0e-5f;
+    return q < KDef<KER>::rmul * KDef<KER>::rmul * (1.0f + kFilterSlack);
+}
+
+// The box [lo, hi] widened by a margin that covers the float rounding of box
+// and node coordinates (relative 1e-6 of the coordinates).
+__device__ __forceinline__ void widen_box(const float lo[3], const float hi[3], float wlo[3],
+                                          float whi[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float m = 1.0e-6f * (fabsf(lo[k]) + fabsf(hi[k])) + 1.0e-30f;
+        wlo[k] = lo[k] - m;
+        whi[k] = hi[k] + m;
+    }
 }
 
 // Warp-cooperative resumable depth-first walk. Emits accepted leaf indices in
@@ -556,7 +567,9 @@ __global__ void __launch_bounds__(kGridThreads, 3) k_grid(GridArgs a) {
     }
     __syncthreads();
     const TileGeom g = tile_setup<TZ>(S, tile);
-    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(S.e, S.uni, node, g.tlo, g.thi); };
+    float wlo[3], whi[3];
+    widen_box(g.tlo, g.thi, wlo, whi);
+    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(S.e, S.uni, node, wlo, whi); };
     const int cx = lane & 15, cy = warp * 2 + (lane >> 4);
     unsigned long long npairs = 0;
     float acc[TZ], sum[TZ], cmp[TZ];
@@ -669,7 +682,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mr_walk(MrArgs a, uint32_t 
     tlo[2] = r.axis[r.nx + r.ny + gz0].x;
     thi[2] = r.axis[r.nx + r.ny + gz0 + nv[2] - 1].x;
     float uni[3] = {r.dp->ell_uniform[0], r.dp->ell_uniform[1], r.dp->ell_uniform[2]};
-    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(S.e, uni, node, tlo, thi); };
+    float wlo[3], whi[3];
+    widen_box(tlo, thi, wlo, whi);
+    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(S.e, uni, node, wlo, whi); };
     int spv;
     int nl = warp_walk_start(S.e.tv, test, S.stack, spv, S.leaves);
     uint32_t total = 0;
@@ -753,7 +768,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
         const RoiDesc &r = S.roi;
         // ---- the tile's node coordinates
         TileGeom g;
-        float isp[3], mlo[3], mhi[3];  // 1 / node spacing; tile box widened by the rounding margin
+        float isp[3], mcen[3], mhw[3];  // 1 / node spacing; tile box widened by the rounding margin
         tile_origin<TZ, kWX, kWY>(r, it.x - r.tile_base, g.gx0, g.gy0, g.gz0, g.nv);
         if (lane < kWX + kWY + TZ) {
             float2 v = make_float2(0.f, 0.f);
@@ -783,8 +798,9 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                 g.sp3[k] = g.nv[k] > 1 ? (S.axt[off[k] + 1].x - S.axt[off[k]].x) : 1.f;
                 isp[k] = g.sp3[k] > 0.f ? 1.0f / g.sp3[k] : 0.f;
                 const float mg = 1.0e-6f * (fabsf(g.tlo[k]) + fabsf(g.thi[k]));
-                mlo[k] = g.tlo[k] - mg;
-                mhi[k] = g.thi[k] + mg;
+                const float lo_m = g.tlo[k] - mg, hi_m = g.thi[k] + mg;
+                mcen[k] = 0.5f * (lo_m + hi_m);
+                mhw[k] = 0.5f * (hi_m - lo_m);
             }
         }
         float acc[TZ], sum[TZ], cmp[TZ];
@@ -822,7 +838,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                         f1[k] = g.nv[k] - 1;
                     }
                     if (f0[k] > f1[k]) acc_pt = false;
-                    const float t = fmaxf(fmaxf(mlo[k] - pc[k], pc[k] - mhi[k]), 0.f) * rl[k];
+                    const float t = fmaxf(fabsf(pc[k] - mcen[k]) - mhw[k], 0.f) * rl[k];
                     qlb = fmaf(t, t, qlb);
                 }
                 if (!(qlb < KDef<KER>::rmul * KDef<KER>::rmul * (1.0f + kFilterSlack))) acc_pt = false;
@@ -1541,21 +1557,22 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
             tlo[k] = fminf(tlo[k], __shfl_xor_sync(0xffffffffu, tlo[k], o));
             thi[k] = fmaxf(thi[k], __shfl_xor_sync(0xffffffffu, thi[k], o));
         }
-    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, s_uni, node, tlo, thi); };
-    // the query box widened by the rounding margin of the per-point filter
-    float mlo[3], mhi[3];
+    // the query box widened by the rounding margin (node test and per-point filter),
+    // the latter as centre and half-width
+    float mlo[3], mhi[3], mcen[3], mhw[3];
+    widen_box(tlo, thi, mlo, mhi);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float mg = 1.0e-6f * (fabsf(tlo[k]) + fabsf(thi[k]));
-        mlo[k] = tlo[k] - mg;
-        mhi[k] = thi[k] + mg;
+        mcen[k] = 0.5f * (mlo[k] + mhi[k]);
+        mhw[k] = 0.5f * (mhi[k] - mlo[k]);
     }
+    auto test = [&](int64_t node) { return node_reaches<KER, BW, CLIP>(a.e, s_uni, node, mlo, mhi); };
 
     float sum = 0.f, cmp = 0.f;
     unsigned long long npairs = 0;
     const f32x2 QX = f2_pack(q.x, q.x), QY = f2_pack(q.y, q.y), QZ = f2_pack(q.z, q.z);
     // entries s and s + 1 (s even) against this lane's query
-    auto pair2 = [&](int s, f32x2 &acc) {
+    auto pair2 = [&](int s, float &acc0, float &acc1) {
         const f32x2 dx = f2_sub(QX, f2_ld(&S.sx[s]));
         const f32x2 dy = f2_sub(QY, f2_ld(&S.sy[s]));
         const f32x2 dz = f2_sub(QZ, f2_ld(&S.sz[s]));
@@ -1568,18 +1585,17 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
             const f32x2 tz = f2_mul(dz, f2_ld(&S.su[2][s]));
             qq = f2_fma(tz, tz, f2_fma(ty, ty, f2_mul(tx, tx)));
         }
-        float q0, q1;
+        float q0, q1, c0, c1;
         f2_unpack(qq, q0, q1);
+        f2_unpack(f2_ld(&S.sc[s]), c0, c1);
         const bool in0 = q0 < KDef<KER>::qmax, in1 = q1 < KDef<KER>::qmax;
-        float w0, w1;
         if (KER == SF_K_GAUSS3) {
-            w0 = in0 ? ex2_approx(-q0) : 0.f;
-            w1 = in1 ? ex2_approx(-q1) : 0.f;
+            if (in0) acc0 = fmaf(c0, ex2_approx(-q0), acc0);
+            if (in1) acc1 = fmaf(c1, ex2_approx(-q1), acc1);
         } else {
-            w0 = in0 ? 1.0f - q0 : 0.f;
-            w1 = in1 ? 1.0f - q1 : 0.f;
+            if (in0) acc0 = fmaf(c0, 1.0f - q0, acc0);
+            if (in1) acc1 = fmaf(c1, 1.0f - q1, acc1);
         }
-        acc = f2_fma(f2_ld(&S.sc[s]), f2_pack(w0, w1), acc);
         if (CNT) npairs += (unsigned)in0 + (unsigned)in1;
     };
     auto add = [&](float v) {  // compensated running sum (TwoSum)
@@ -1638,7 +1654,7 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
                 float qlb = 0.f;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const float t = fmaxf(fmaxf(mlo[k] - pc[k], pc[k] - mhi[k]), 0.f) * r[k];
+                    const float t = fmaxf(fabsf(pc[k] - mcen[k]) - mhw[k], 0.f) * r[k];
                     qlb = fmaf(t, t, qlb);
                 }
                 ok = ok && qlb < KDef<KER>::rmul * KDef<KER>::rmul * (1.0f + kFilterSlack);
@@ -1662,14 +1678,14 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
             cnt += __popc(m);
             if (cnt >= kLeaf) {  // warp-uniform: a full half of the ring is staged
                 __syncwarp();
-                f32x2 acc[2] = {0ull, 0ull};
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-                for (int e = 0; e < kLeaf; e += 2) pair2(head + e, acc[(e >> 1) & 1]);
+                for (int e = 0; e < kLeaf; e += 4) {
+                    pair2(head + e, a0, a1);
+                    pair2(head + e + 2, a2, a3);
+                }
                 head ^= kLeaf;
                 cnt -= kLeaf;
-                float a0, a1, a2, a3;
-                f2_unpack(acc[0], a0, a1);
-                f2_unpack(acc[1], a2, a3);
                 add((a0 + a1) + (a2 + a3));
                 __syncwarp();
             }
@@ -1687,11 +1703,9 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
     }
     __syncwarp();
     if (cnt > 0) {
-        f32x2 acc = 0ull;
-        for (int e = 0; e < cnt; e += 2) pair2(head + e, acc);
+        float a0 = 0.f, a1 = 0.f;
+        for (int e = 0; e < cnt; e += 2) pair2(head + e, a0, a1);
         if (CNT && (cnt & 1)) --npairs;  // the padding entry is "in support" (q = 0)
-        float a0, a1;
-        f2_unpack(acc, a0, a1);
         add(a0 + a1);
     }
     if (active) a.rho_sorted[qi] = (float)(((double)sum + (double)cmp) * s_inv);
@@ -1818,7 +1832,9 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points_tc(PointsArgs a) {
         xsq[sl] = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
     }
     float uni[3] = {0.f, 0.f, 0.f};
-    auto test = [&](int64_t node) { return node_reaches<KER, BW_ISO, CLIP>(a.e, uni, node, tlo, thi); };
+    float wlo[3], whi[3];
+    widen_box(tlo, thi, wlo, whi);
+    auto test = [&](int64_t node) { return node_reaches<KER, BW_ISO, CLIP>(a.e, uni, node, wlo, whi); };
 
     float acc[4] = {0.f, 0.f, 0.f, 0.f}, sum[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
     int spv;
