@@ -15,12 +15,13 @@
 //     compacted once into a per-warp buffer in global memory (L2-resident);
 //  3. histogram while collecting: per lane, 32 bins of FP32 d2 over [0, T];
 //     the bin holding the k-th is found;
-//  4. band pass: points clearly below the bin are in; the few whose FP32 d2 lies
-//     within a relative 2e-6 of the bin are re-evaluated in FP64 (no FMA
-//     contraction) and ranked by (d2, original index). If a band overflows its
-//     buffer the bin is split again (the band pass has already binned the
-//     bracket for that round); at FP32 resolution (exact duplicates) the
-//     remaining members are extracted one by one.
+//  4. band pass: points clearly below the bin are in; the ones whose FP32 d2
+//     lies in the bin (widened by a relative 2e-6) are re-evaluated in FP64 (no
+//     FMA contraction) into a per-lane buffer of 64 in global memory and ranked
+//     by (d2, original index) -- one pass resolves almost every lane. If a band
+//     overflows its buffer the bin is split again (the band pass has already
+//     binned the bracket for that round); at FP32 resolution (exact duplicates)
+//     the remaining members are extracted one by one.
 // FP32 d2 carries a relative error below 5 * 2^-24, so the 2e-6 margins make
 // every in/out decision outside the band exact. If a warp's candidates exceed
 // its buffer, its passes walk the index again instead (same result, slower).
@@ -30,7 +31,7 @@ namespace sf {
 
 constexpr int kKnnWarps = 4;
 constexpr int kNB = 32;        // histogram bins per lane
-constexpr int kBand = 4;       // band buffer per lane (small: shared memory sets the occupancy)
+constexpr int kBand = 64;      // band buffer per lane (global memory, interleaved by lane)
 constexpr int kCand = 64;      // candidate leaves per walk batch
 constexpr int kCache = 32768;  // candidate points per warp buffer (global)
 constexpr int kKStack = 32 * kMaxLevels;
@@ -42,8 +43,6 @@ struct KnnWarpSmem {
     float4 blo[32], bhi[32];   // child boxes under test
     float4 pts[kLeaf];         // staged candidates (x, y, z, original id bits)
     uint32_t hist[kNB][32];
-    double bd[kBand][32];
-    uint32_t bi[kBand][32];
 };
 
 struct KnnArgs {
@@ -53,6 +52,8 @@ struct KnnArgs {
     float *h_sorted;          // out: h per sorted point
     uint32_t *nbr_orig;       // out (nullable): [n][k] by original index
     float4 *cache;            // [slots][kCache] candidate buffers
+    double *band_d;           // [slots][kBand][32] band members' FP64 d2
+    uint32_t *band_i;         // [slots][kBand][32] band members' original ids
     unsigned int *next_leaf;  // work counter (zeroed before launch)
 };
 
@@ -245,7 +246,8 @@ struct KnnWarp {
     }
 };
 
-__device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_t leaf) {
+__device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, double *bd, uint32_t *bi,
+                         int64_t leaf) {
     const int lane = threadIdx.x & 31;
     const TreeView &tv = a.tv;
     const int k = a.k;
@@ -400,8 +402,8 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
                         ++nbelow;
                     } else {
                         if (nband < kBand) {
-                            S.bd[nband][lane] = d2_f64(q, p);
-                            S.bi[nband][lane] = id;
+                            bd[nband * 32 + lane] = d2_f64(q, p);
+                            bi[nband * 32 + lane] = id;
                         }
                         ++nband;
                     }
@@ -416,19 +418,19 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
             nb_below = nbelow;
             if (nband <= kBand) {
                 for (int x = 1; x < nband; ++x) {
-                    const double dv = S.bd[x][lane];
-                    const uint32_t iv = S.bi[x][lane];
+                    const double dv = bd[x * 32 + lane];
+                    const uint32_t iv = bi[x * 32 + lane];
                     int y = x - 1;
-                    while (y >= 0 && key_less(dv, iv, S.bd[y][lane], S.bi[y][lane])) {
-                        S.bd[y + 1][lane] = S.bd[y][lane];
-                        S.bi[y + 1][lane] = S.bi[y][lane];
+                    while (y >= 0 && key_less(dv, iv, bd[y * 32 + lane], bi[y * 32 + lane])) {
+                        bd[(y + 1) * 32 + lane] = bd[y * 32 + lane];
+                        bi[(y + 1) * 32 + lane] = bi[y * 32 + lane];
                         --y;
                     }
-                    S.bd[y + 1][lane] = dv;
-                    S.bi[y + 1][lane] = iv;
+                    bd[(y + 1) * 32 + lane] = dv;
+                    bi[(y + 1) * 32 + lane] = iv;
                 }
                 const int pick = min(max(need, 1), min(nband, kBand)) - 1;
-                kth = S.bd[pick][lane];
+                kth = bd[pick * 32 + lane];
                 done = true;
             } else if (round == 7 || !(e_hi - e_lo > 4.0f * kDelta * e_hi)) {
                 extract = true;  // bin cannot shrink further (or out of rounds)
@@ -490,22 +492,25 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, int64_
         });
         if (valid && !extract)
             for (int x = 0; x < need && x < kBand && slot + x < k; ++x)
-                a.nbr_orig[(int64_t)qid * k + slot + x] = S.bi[x][lane];
+                a.nbr_orig[(int64_t)qid * k + slot + x] = bi[x * 32 + lane];
     }
 }
 
-__global__ void __launch_bounds__(kKnnWarps * 32, 6) k_knn(KnnArgs a) {
+__global__ void __launch_bounds__(kKnnWarps * 32, 7) k_knn(KnnArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
     KnnWarpSmem &S = reinterpret_cast<KnnWarpSmem *>(smem_raw)[warp];
-    float4 *cache = a.cache + ((int64_t)blockIdx.x * kKnnWarps + warp) * kCache;
+    const int64_t slot = (int64_t)blockIdx.x * kKnnWarps + warp;
+    float4 *cache = a.cache + slot * kCache;
+    double *bd = a.band_d + slot * (kBand * 32);
+    uint32_t *bi = a.band_i + slot * (kBand * 32);
     const int64_t nleaf = a.tv.cnt[0];
     while (true) {
         unsigned int leaf = 0;
         if ((threadIdx.x & 31) == 0) leaf = atomicAdd(a.next_leaf, 1u);
         leaf = __shfl_sync(0xffffffffu, leaf, 0);
         if ((int64_t)leaf >= nleaf) break;
-        knn_leaf(a, S, cache, (int64_t)leaf);
+        knn_leaf(a, S, cache, bd, bi, (int64_t)leaf);
     }
 }
 
@@ -552,6 +557,8 @@ sf_status knn_run(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_sorted,
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, need_blocks));
     Scratch sc(s);
     a.cache = sc.get<float4>(blocks * kKnnWarps * (int64_t)kCache);
+    a.band_d = sc.get<double>(blocks * kKnnWarps * (int64_t)kBand * 32);
+    a.band_i = sc.get<uint32_t>(blocks * kKnnWarps * (int64_t)kBand * 32);
     a.next_leaf = sc.get<unsigned int>(1);
     SF_TRY_SCRATCH(sc);
     SF_TRY_CUDA(cudaMemsetAsync(a.next_leaf, 0, sizeof(unsigned int), s));
