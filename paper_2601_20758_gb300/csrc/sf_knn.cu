@@ -11,8 +11,9 @@
 //     the next leaves in sorted order, bracketed by two rounds of 32-bin
 //     histograms -- an upper bound of the true k-th distance;
 //  2. candidates: the index walk keeps the leaves within that radius of at
-//     least one lane's point; their points inside the warp's envelope box are
-//     compacted once into a per-warp buffer in global memory (L2-resident);
+//     least one lane's point, and records them in a per-warp leaf list in
+//     global memory; their points inside the warp's envelope box are the
+//     candidates (every pass reloads them leaf by leaf);
 //  3. histogram while collecting: per lane, 32 bins of FP32 d2 over [0, T];
 //     the bin holding the k-th is found;
 //  4. band pass: points clearly below the bin are in; the ones whose FP32 d2
@@ -23,8 +24,8 @@
 //     binned the bracket for that round); at FP32 resolution (exact duplicates)
 //     the remaining members are extracted one by one.
 // FP32 d2 carries a relative error below 5 * 2^-24, so the 2e-6 margins make
-// every in/out decision outside the band exact. If a warp's candidates exceed
-// its buffer, its passes walk the index again instead (same result, slower).
+// every in/out decision outside the band exact. If a warp's accepted leaves
+// exceed its list, its passes walk the index again instead (same result).
 #include "sf_internal.cuh"
 
 namespace sf {
@@ -33,7 +34,7 @@ constexpr int kKnnWarps = 4;
 constexpr int kNB = 32;        // histogram bins per lane
 constexpr int kBand = 64;      // band buffer per lane (global memory, interleaved by lane)
 constexpr int kCand = 64;      // candidate leaves per walk batch
-constexpr int kCache = 32768;  // candidate points per warp buffer (global)
+constexpr int kLeafList = 4096;  // accepted leaves recorded per warp (global)
 constexpr int kKStack = 32 * kMaxLevels;
 constexpr float kDelta = 2.0e-6f;
 
@@ -51,7 +52,7 @@ struct KnnArgs {
     int k;
     float *h_sorted;          // out: h per sorted point
     uint32_t *nbr_orig;       // out (nullable): [n][k] by original index
-    float4 *cache;            // [slots][kCache] candidate buffers
+    int *leaf_list;           // [slots][kLeafList] accepted leaves of the current query leaf
     double *band_d;           // [slots][kBand][32] band members' FP64 d2
     uint32_t *band_i;         // [slots][kBand][32] band members' original ids
     unsigned int *next_leaf;  // work counter (zeroed before launch)
@@ -79,15 +80,15 @@ struct KnnWarp {
     const TreeView &tv;
     const uint32_t *perm;
     KnnWarpSmem &S;
-    float4 *cache;
+    int *leaf_list;  // this warp's recorded leaves
     float4 q;
     float r2;
     float env_lo[3], env_hi[3];  // warp envelope of all balls
-    int ncache;
+    int nlist;
     bool overflow;
 
-    __device__ KnnWarp(const TreeView &t, const uint32_t *p, KnnWarpSmem &s, float4 *c)
-        : tv(t), perm(p), S(s), cache(c) {}
+    __device__ KnnWarp(const TreeView &t, const uint32_t *p, KnnWarpSmem &s, int *c)
+        : tv(t), perm(p), S(s), leaf_list(c) {}
 
     // Mask of the children (lane c holds child c at level cl) within the ball
     // of at least one lane. Conservative: relative slack 1e-5.
@@ -164,11 +165,40 @@ struct KnnWarp {
         return 0;
     }
 
-    // Visit the envelope-filtered points of every accepted leaf, 32 at a time:
+    // Stage the envelope-filtered points of the leaves S.cand[0..nl), one leaf
+    // at a time (the next leaf's points load while the current one is used):
     // chunk(n) is called with S.pts[0..n) staged (x, y, z, original id bits).
     template <typename Chunk>
-    __device__ void walk_points(Chunk chunk) {
+    __device__ __forceinline__ void visit(int nl, Chunk chunk) {
         const int lane = threadIdx.x & 31;
+        float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t idn = 0;
+        auto load = [&](int li) {
+            const int64_t j = (int64_t)S.cand[li] * kLeaf + lane;
+            if (j < tv.n) {
+                pn = __ldg(&tv.pos[j]);
+                idn = __ldg(&perm[j]);
+            }
+        };
+        if (nl > 0) load(0);
+        for (int li = 0; li < nl; ++li) {
+            const int64_t j = (int64_t)S.cand[li] * kLeaf + lane;
+            float4 p = pn;
+            p.w = __uint_as_float(idn);
+            if (li + 1 < nl) load(li + 1);
+            const bool in = j < tv.n && p.x >= env_lo[0] && p.x <= env_hi[0] && p.y >= env_lo[1] &&
+                            p.y <= env_hi[1] && p.z >= env_lo[2] && p.z <= env_hi[2];
+            const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (in) S.pts[__popc(m & ((1u << lane) - 1u))] = p;
+            __syncwarp();
+            chunk(__popc(m));
+            __syncwarp();
+        }
+    }
+
+    // Every accepted leaf by walking the index.
+    template <typename Chunk>
+    __device__ __forceinline__ void walk_points(Chunk chunk) {
         int sp;
         int nl = start(sp);
         while (true) {
@@ -177,83 +207,72 @@ struct KnnWarp {
                 nl = walk(sp);
                 if (nl == 0) break;
             }
-            for (int li = 0; li < nl; ++li) {
-                const int64_t j = (int64_t)S.cand[li] * kLeaf + lane;
-                bool in = false;
-                float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < tv.n) {
-                    p = __ldg(&tv.pos[j]);
-                    p.w = __uint_as_float(__ldg(&perm[j]));
-                    in = p.x >= env_lo[0] && p.x <= env_hi[0] && p.y >= env_lo[1] &&
-                         p.y <= env_hi[1] && p.z >= env_lo[2] && p.z <= env_hi[2];
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, in);
-                if (in) S.pts[__popc(m & ((1u << lane) - 1u))] = p;
-                __syncwarp();
-                chunk(__popc(m));
-                __syncwarp();
-            }
+            visit(nl, chunk);
             nl = 0;
         }
     }
 
-    // Fill the global candidate buffer once; fn(n) sees each staged chunk
-    // S.pts[0..n) on the way (all lanes together).
+    // Walk once, recording the accepted leaves in the warp's global leaf list;
+    // fn(n) sees each staged chunk S.pts[0..n) on the way (all lanes together).
     template <typename Fn>
-    __device__ void collect(Fn fn) {
+    __device__ __forceinline__ void collect(Fn fn) {
         const int lane = threadIdx.x & 31;
-        ncache = 0;
+        nlist = 0;
         overflow = false;
-        walk_points([&](int n) {
-            fn(n);
-            if (ncache + n <= kCache) {
-                if (lane < n) cache[ncache + lane] = S.pts[lane];
-            } else {
-                overflow = true;
+        int sp;
+        int nl = start(sp);
+        while (true) {
+            if (nl == 0) {
+                if (sp == 0) break;
+                nl = walk(sp);
+                if (nl == 0) break;
             }
-            ncache += n;
-        });
+            for (int i = lane; i < nl; i += 32)
+                if (nlist + i < kLeafList) leaf_list[nlist + i] = S.cand[i];
+            if (nlist + nl > kLeafList) overflow = true;
+            nlist += nl;
+            visit(nl, fn);
+            nl = 0;
+        }
         __syncwarp();
     }
 
-    // fn(point with id bits in w) for every candidate, all lanes together.
+    // fn(point with id bits in w) for every candidate, all lanes together: the
+    // recorded leaves again (or a fresh walk if the list overflowed).
     template <typename Fn>
-    __device__ void each(Fn fn) {
+    __device__ __forceinline__ void each(Fn fn) {
         const int lane = threadIdx.x & 31;
+        auto per_chunk = [&](int n) {
+            int t = 0;
+            for (; t + 2 <= n; t += 2) {
+                const float4 a = S.pts[t], b = S.pts[t + 1];
+                fn(a);
+                fn(b);
+            }
+            if (t < n) fn(S.pts[t]);
+        };
         if (!overflow) {
-            // the next chunk is loaded while the current one is processed
-            float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (lane < ncache) nxt = cache[lane];
-            for (int base = 0; base < ncache; base += 32) {
-                const int n = min(32, ncache - base);
-                if (lane < n) S.pts[lane] = nxt;
+            for (int base = 0; base < nlist; base += kCand) {
+                const int nb = min(kCand, nlist - base);
                 __syncwarp();
-                if (base + 32 + lane < ncache) nxt = cache[base + 32 + lane];
-                int t = 0;
-                for (; t + 2 <= n; t += 2) {
-                    const float4 a = S.pts[t], b = S.pts[t + 1];
-                    fn(a);
-                    fn(b);
-                }
-                if (t < n) fn(S.pts[t]);
+                for (int i = lane; i < nb; i += 32) S.cand[i] = leaf_list[base + i];
                 __syncwarp();
+                visit(nb, per_chunk);
             }
             return;
         }
-        walk_points([&](int n) {
-            for (int t = 0; t < n; ++t) fn(S.pts[t]);
-        });
+        walk_points(per_chunk);
     }
 };
 
-__device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, float4 *cache, double *bd, uint32_t *bi,
+__device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, double *bd, uint32_t *bi,
                          int64_t leaf) {
     const int lane = threadIdx.x & 31;
     const TreeView &tv = a.tv;
     const int k = a.k;
     const int64_t qi = leaf * kLeaf + lane;
     const bool valid = qi < tv.n;
-    KnnWarp W(tv, a.perm, S, cache);
+    KnnWarp W(tv, a.perm, S, leaf_list);
     W.q = valid ? __ldg(&tv.pos[qi]) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 q = W.q;
     const uint32_t qid = valid ? __ldg(&a.perm[qi]) : 0u;
@@ -501,7 +520,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32, 7) k_knn(KnnArgs a) {
     const int warp = threadIdx.x >> 5;
     KnnWarpSmem &S = reinterpret_cast<KnnWarpSmem *>(smem_raw)[warp];
     const int64_t slot = (int64_t)blockIdx.x * kKnnWarps + warp;
-    float4 *cache = a.cache + slot * kCache;
+    int *leaf_list = a.leaf_list + slot * kLeafList;
     double *bd = a.band_d + slot * (kBand * 32);
     uint32_t *bi = a.band_i + slot * (kBand * 32);
     const int64_t nleaf = a.tv.cnt[0];
@@ -510,7 +529,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32, 7) k_knn(KnnArgs a) {
         if ((threadIdx.x & 31) == 0) leaf = atomicAdd(a.next_leaf, 1u);
         leaf = __shfl_sync(0xffffffffu, leaf, 0);
         if ((int64_t)leaf >= nleaf) break;
-        knn_leaf(a, S, cache, bd, bi, (int64_t)leaf);
+        knn_leaf(a, S, leaf_list, bd, bi, (int64_t)leaf);
     }
 }
 
@@ -556,7 +575,7 @@ sf_status knn_run(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_sorted,
     const int64_t need_blocks = (idx->cnt[0] + kKnnWarps - 1) / kKnnWarps;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, need_blocks));
     Scratch sc(s);
-    a.cache = sc.get<float4>(blocks * kKnnWarps * (int64_t)kCache);
+    a.leaf_list = sc.get<int>(blocks * kKnnWarps * (int64_t)kLeafList);
     a.band_d = sc.get<double>(blocks * kKnnWarps * (int64_t)kBand * 32);
     a.band_i = sc.get<uint32_t>(blocks * kKnnWarps * (int64_t)kBand * 32);
     a.next_leaf = sc.get<unsigned int>(1);
