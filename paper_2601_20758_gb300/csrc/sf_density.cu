@@ -55,36 +55,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-// Packed FP32 pairs (two IEEE single-precision lanes per 64-bit register,
-// one instruction for both; each lane rounds exactly like the scalar op).
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 f2_pack(float a, float b) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(f32x2 v, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
-    f32x2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ f32x2 f2_ld(const float *p) {  // 8-byte aligned
-    return *reinterpret_cast<const f32x2 *>(p);
-}
-
 // Squared-support slack of the filters (covers the reciprocal's error and the
 // rounding of the gap terms; the filters only ever admit too much).
 constexpr float kFilterSlack = 3.0e-5f;
