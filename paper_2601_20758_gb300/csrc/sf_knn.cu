@@ -8,8 +8,9 @@
 // Persistent warps; each takes the next leaf of 32 Morton-consecutive query
 // points from an atomic counter (no warp waits for another):
 //  1. radius bound: per lane, the k-th smallest FP32 d2 among the points of
-//     the next leaves in sorted order, bracketed by two rounds of 32-bin
-//     histograms -- an upper bound of the true k-th distance;
+//     nearby leaves in sorted order (a bin edge above it, from 32-bin
+//     histograms of 5 then 13 leaves at k = 64) -- an upper bound of the true
+//     k-th distance;
 //  2. candidates: the index walk keeps the leaves within that radius of at
 //     least one lane's point, and records them in a per-warp leaf list in
 //     global memory; their points inside the warp's envelope box are the
@@ -284,19 +285,26 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, doubl
 
     // ---- 1. radius bound from the neighbouring leaves in sorted order
     const int64_t nleaf = tv.cnt[0];
-    const int64_t wl = (int64_t)((k + 1 + 31) / 32) + 10;  // 13 leaves at k = 64 (a wider window gives a tighter bound)
-    int64_t w0 = leaf - wl / 2, w1;
-    if (w0 < 0) w0 = 0;
-    w1 = w0 + wl - 1;
-    if (w1 >= nleaf) {
-        w1 = nleaf - 1;
-        w0 = w1 - wl + 1 < 0 ? 0 : w1 - wl + 1;
-    }
-    // first bracket: the farthest corner of the window leaves' joint box
+    // a central window of (k + 1)/32 + 2 leaves brackets the bound, the full
+    // window of (k + 1)/32 + 10 leaves (13 at k = 64) tightens it: any subset of
+    // the other points gives an upper bound, more nearby points a tighter one
+    auto window = [&](int64_t wl, int64_t &w0, int64_t &w1) {
+        w0 = leaf - wl / 2;
+        if (w0 < 0) w0 = 0;
+        w1 = w0 + wl - 1;
+        if (w1 >= nleaf) {
+            w1 = nleaf - 1;
+            w0 = w1 - wl + 1 < 0 ? 0 : w1 - wl + 1;
+        }
+    };
+    int64_t c0, c1, w0, w1;
+    window((int64_t)((k + 1 + 31) / 32) + 2, c0, c1);
+    window((int64_t)((k + 1 + 31) / 32) + 10, w0, w1);
+    // first bracket: the farthest corner of the central leaves' joint box
     float whi = 0.f;
     {
         float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int64_t L = w0; L <= w1; ++L) {
+        for (int64_t L = c0; L <= c1; ++L) {
             const float4 lo = __ldg(&tv.nlo[L]), hi = __ldg(&tv.nhi[L]);
             blo[0] = fminf(blo[0], lo.x); blo[1] = fminf(blo[1], lo.y); blo[2] = fminf(blo[2], lo.z);
             bhi[0] = fmaxf(bhi[0], hi.x); bhi[1] = fmaxf(bhi[1], hi.y); bhi[2] = fmaxf(bhi[2], hi.z);
@@ -305,8 +313,8 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, doubl
                     dz = fmaxf(q.z - blo[2], bhi[2] - q.z);
         whi = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) * (1.0f + 1.0e-5f);
     }
-    auto window_visit = [&](auto fn) {
-        for (int64_t L = w0; L <= w1; ++L) {
+    auto window_visit = [&](int64_t L0, int64_t L1, auto fn) {
+        for (int64_t L = L0; L <= L1; ++L) {
             const int64_t base = L * kLeaf;
             if (base + lane < tv.n) S.pts[lane] = __ldg(&tv.pos[base + lane]);
             __syncwarp();
@@ -315,13 +323,15 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, doubl
             __syncwarp();
         }
     };
-    float wlo = 0.f;
-    for (int round = 0; round < 2; ++round) {  // two rounds: the bound is then within 0.1% of the window k-th
+    // round 0: the central leaves over [0, whi]; round 1: all window leaves over
+    // [0, the central k-th's bin] (their k-th is no larger)
+    for (int round = 0; round < 2; ++round) {
+        float wlo = 0.f;
         clear_hist();
         const float width = whi - wlo;
         const float inv = width > 0.f ? (float)kNB / width : 0.f;
         int below = 0;
-        window_visit([&](float4 p, int64_t j) {
+        window_visit(round == 0 ? c0 : w0, round == 0 ? c1 : w1, [&](float4 p, int64_t j) {
             if (j != qi) {
                 const float d = d2_f32(q, p);
                 if (d < wlo) ++below;
@@ -337,10 +347,8 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, doubl
         }
         // keep the current bracket if rounding left the k-th outside it
         if (b < kNB && width > 0.f) {
-            const float nlo = (wlo + (float)b * (width / (float)kNB)) * (1.0f - 1.0e-6f);
             const float nhi = (b == kNB - 1 ? whi : wlo + (float)(b + 1) * (width / (float)kNB)) *
                               (1.0f + 1.0e-6f);
-            wlo = fmaxf(nlo, 0.f);
             whi = fminf(nhi, whi);
         }
     }
