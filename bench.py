@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop sample")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-vs-plain comparison over 64 uneven ROIs")
+    ap.add_argument("--no-prec", action="store_true",
+                    help="skip the tensor-core precision variants of the point densities")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--no-count", action="store_true",
                     help="skip the pair-counting pass (value and roofline become null)")
@@ -357,6 +359,11 @@ def main():
     if not args.no_batch:
         batched = run_batched(args, L, torch, d_xyz, p, stream)
 
+    # ---- tensor-core precision variants of the point densities (ROI 1)
+    precision = None
+    if not args.no_prec:
+        precision = run_precision(L, torch, d_xyz, p, boxes[1], stream)
+
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -381,6 +388,7 @@ def main():
                 "kernels_ms_per_roi": {k: v.get("per_roi_ms") for k, v in kern.items() if "per_roi_ms" in v},
                 "serving": serving,
                 "batched": batched,
+                "precision": precision,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -534,6 +542,44 @@ def run_batched(args, L, torch, d_xyz, p, stream):
             "plain_ms": res["plain"], "batched_ms": res["batched"],
             "speedup": res["plain"] / res["batched"], "tile_z": tz, "items_per_warp": ips,
             "tuning_ms": tms, "max_rel_diff_vs_plain": diff}
+
+
+def run_precision(L, torch, d_xyz, p, box, stream):
+    """Point densities of one ROI with the FP32 path and the tensor-core cross-term
+    variants: device time (CUDA events) and the largest relative deviation from
+    the FP32 densities over points above 1e-3 of the maximum (the errors against
+    the FP64 oracle are measured by tests/test_gpu_tensor.py)."""
+    n = d_xyz.shape[0]
+    idx = L.sf_build_index(d_xyz, stream)
+    out = {}
+    try:
+        L.sf_bandwidths(idx, p, stream)
+        ref = None
+        for name, prec in (("fp32", L.SF_PREC_FP32), ("tf32", L.SF_PREC_TF32),
+                           ("3xtf32", L.SF_PREC_3XTF32), ("bf16", L.SF_PREC_BF16)):
+            q = L.make_params(rule=L.SF_BW_KNN, k=K_NN, scope=L.SF_SCOPE_GLOBAL)
+            q.prec = prec
+            dens = torch.empty(n, device="cuda")
+            ids = torch.empty(n, dtype=torch.int32, device="cuda")
+            cnt = L.sf_kde_points(idx, box, None, L.SF_K_GAUSS3, q, dens, ids, stream=stream)
+            ms = []
+            for _ in range(3):
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                L.sf_kde_points(idx, box, None, L.SF_K_GAUSS3, q, dens, ids, stream=stream)
+                z.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(z))
+            d = dens[:cnt].double()
+            if ref is None:
+                ref = d
+            big = ref >= 1e-3 * ref.max()
+            dev = float(((d - ref).abs()[big] / ref[big]).max()) if name != "fp32" else 0.0
+            out[name] = {"ms": sorted(ms)[1], "max_rel_vs_fp32": dev}
+        out["points"] = int(cnt)
+    finally:
+        L.sf_free_index(idx)
+    return out
 
 
 def run_e2e(args, L, torch, xyz, boxes, p, pairs_step, stream, world, barrier, dist):

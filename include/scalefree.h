@@ -72,9 +72,10 @@ enum { SF_SCOPE_CLIP = 0, SF_SCOPE_GLOBAL = 1 };
 
 /* Precision of the point densities (sf_kde_points, DIRECT, kNN bandwidths):
  * FP32 everywhere, or the squared-distance cross term on tensor cores in TF32
- * (one pass) or 3xTF32 (hi/lo split, three passes); see sf_kde_points. Grids
- * and every other call are FP32 only. */
-enum { SF_PREC_FP32 = 0, SF_PREC_TF32 = 1, SF_PREC_3XTF32 = 2 };
+ * (one pass), 3xTF32 (hi/lo split, three passes) or BF16 (one pass, 8
+ * significant bits); see sf_kde_points. Grids and every other call are FP32
+ * only. */
+enum { SF_PREC_FP32 = 0, SF_PREC_TF32 = 1, SF_PREC_3XTF32 = 2, SF_PREC_BF16 = 3 };
 
 /* Point densities: DIRECT evaluates the kernel sum at each point (self term
  * included); INTERP interpolates the ROI grid trilinearly (Sec. 3.1, last step). */
@@ -94,7 +95,7 @@ typedef struct {
     double p_lo, p_hi;   /* SF_BW_MBE: percentiles of Eq. 1 (paper: 20, 80)      */
     double log_base;     /* SF_BW_MBE: base of the log in Eq. 1; <= 0 means e    */
     int32_t scope;       /* SF_SCOPE_*                                           */
-    int32_t prec;        /* SF_PREC_FP32                                         */
+    int32_t prec;        /* SF_PREC_* (non-FP32: sf_kde_points only)             */
     int32_t points_mode; /* SF_POINTS_*                                          */
     int32_t reserved;    /* must be 0                                            */
 } sf_params;
@@ -186,12 +187,13 @@ sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], i
  * count exceeds capacity, CAPACITY is returned and nothing is written.
  * DIRECT sums the kernels at each point (the point's own kernel included);
  * INTERP interpolates the grid of the same dims trilinearly.
- * params->prec TF32 / 3XTF32 (DIRECT with kNN bandwidths only): the cross term
- * -2 x.y of each squared distance, in coordinates centred on each group of 32
- * query points, runs on the tensor cores; the relative error of q = d^2/h^2 is
- * about 2^-10 (TF32) or 2^-21 (3xTF32) times (|x| + |y|)^2 / d^2, so TF32
- * densities carry errors of order 1e-3 to 1e-2 and 3xTF32 ones of order 1e-5;
- * near the cutoff a pair may fall on either side. dims is used by
+ * params->prec TF32 / 3XTF32 / BF16 (DIRECT with kNN bandwidths only): the
+ * cross term -2 x.y of each squared distance, in coordinates centred on each
+ * group of 32 query points, runs on the tensor cores; the relative error of
+ * q = d^2/h^2 is about 2^-10 (TF32), 2^-21 (3xTF32) or 2^-8 (BF16) times
+ * (|x| + |y|)^2 / d^2, so TF32 densities carry errors of order 1e-2, 3xTF32
+ * ones of order 1e-5 and BF16 ones of order 1e-1; near the cutoff a pair may
+ * fall on either side. dims is used by
  * INTERP and by rule MBE (whose smoothing lengths depend on the grid spacing);
  * it may be NULL otherwise.
  */

@@ -35,6 +35,7 @@ SF_SCOPE_GLOBAL = 1
 SF_PREC_FP32 = 0
 SF_PREC_TF32 = 1
 SF_PREC_3XTF32 = 2
+SF_PREC_BF16 = 3
 SF_POINTS_DIRECT = 0
 SF_POINTS_INTERP = 1
 

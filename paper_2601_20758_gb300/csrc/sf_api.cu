@@ -97,7 +97,8 @@ static sf_status check_params(const sf_index *idx, const sf_params *p, int kerne
         return fail(SF_ERR_INVALID_ARG, "%s: unknown kernel %d", fn, kernel);
     if (p->scope != SF_SCOPE_CLIP && p->scope != SF_SCOPE_GLOBAL)
         return fail(SF_ERR_INVALID_ARG, "%s: unknown scope %d", fn, p->scope);
-    if (p->prec != SF_PREC_FP32 && p->prec != SF_PREC_TF32 && p->prec != SF_PREC_3XTF32)
+    if (p->prec != SF_PREC_FP32 && p->prec != SF_PREC_TF32 && p->prec != SF_PREC_3XTF32 &&
+        p->prec != SF_PREC_BF16)
         return fail(SF_ERR_INVALID_ARG, "%s: unsupported precision %d", fn, p->prec);
     if (p->points_mode != SF_POINTS_DIRECT && p->points_mode != SF_POINTS_INTERP)
         return fail(SF_ERR_INVALID_ARG, "%s: unknown points_mode %d", fn, p->points_mode);
@@ -291,7 +292,7 @@ sf_status sf_kde_points(sf_index *idx, const sf_box *roi, const int32_t *dims, i
     SF_TRY(prepare(idx, *roi, need_grid ? &g : nullptr, kernel, *params, sc, pr, s));
     if (params->prec != SF_PREC_FP32 &&
         (params->rule != SF_BW_KNN || params->points_mode != SF_POINTS_DIRECT))
-        return fail(SF_ERR_INVALID_ARG, "sf_kde_points: TF32 / 3xTF32 need rule KNN and DIRECT");
+        return fail(SF_ERR_INVALID_ARG, "sf_kde_points: TF32 / 3xTF32 / BF16 need rule KNN and DIRECT");
     if (params->prec != SF_PREC_FP32) {
         SF_TRY(density_points_tc(idx, *roi, pr.call, params->prec, rho, inroi, s));
     } else if (params->points_mode == SF_POINTS_INTERP) {

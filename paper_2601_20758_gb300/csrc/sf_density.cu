@@ -1719,7 +1719,8 @@ static cudaError_t dispatch_points(int bw, bool clip, const PointsArgs &a, int64
 // distance of query i and candidate j is |x_i|^2 + |y_j|^2 - 2 x_i . y_j; the
 // cross term of a 32 x 32 block is a [32 x 8] . [8 x 32] product (features x,
 // y, z, zero-padded) done by mma.sync m16n8k8 in TF32 (or as the 3-pass
-// hi/lo split, "3xTF32", accurate to about 2^-21 of |x||y|); the squared norms,
+// hi/lo split, "3xTF32", accurate to about 2^-21 of |x||y|), or m16n8k16 in
+// BF16 (8 significant bits); the squared norms,
 // the scaling by 1/h^2, the cutoff, the kernel and the compensated sums stay
 // in FP32. Isotropic bandwidths only (the kNN rule).
 // ---------------------------------------------------------------------------
@@ -1737,6 +1738,28 @@ __device__ __forceinline__ void mma_tf32(float d[4], uint32_t a0, uint32_t a1, u
         "{%8,%9}, {%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a0), "r"(a1), "r"(z), "r"(z), "r"(b0), "r"(z));
+}
+
+// BF16: m16n8k16 with the features in k = 0..3 (pairs (x, y), (z, 0) in the
+// lanes with tig 0 and 1), k = 4..15 zero. a0 / a1: rows g / g + 8, b0: column g.
+__device__ __forceinline__ void mma_bf16(float d[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(z), "r"(z), "r"(b0), "r"(z));
+}
+
+// The TF32 fragment layout holds feature tig of a row in lane (g, tig); the BF16
+// one wants features (2 tig, 2 tig + 1) packed in that lane (zero for tig >= 2).
+__device__ __forceinline__ uint32_t bf16_pair_from_tf32_layout(float f) {
+    const int lane = threadIdx.x & 31, tig = lane & 3;
+    const float lo = __shfl_sync(0xffffffffu, f, (lane & ~3) | ((2 * tig) & 3));
+    const float hi = __shfl_sync(0xffffffffu, f, (lane & ~3) | ((2 * tig + 1) & 3));
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(tig < 2 ? hi : 0.f), "f"(tig < 2 ? lo : 0.f));
+    return r;
 }
 
 template <int PREC>
@@ -1801,6 +1824,11 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points_tc(PointsArgs a) {
         feat[sl] = tig == 0 ? rx : (tig == 1 ? ry : (tig == 2 ? rz : 0.f));
         xsq[sl] = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
     }
+    uint32_t fa16[4] = {0u, 0u, 0u, 0u};  // BF16 A fragments of the four rows
+    if (PREC == SF_PREC_BF16) {
+#pragma unroll
+        for (int sl = 0; sl < 4; ++sl) fa16[sl] = bf16_pair_from_tf32_layout(feat[sl]);
+    }
     float uni[3] = {0.f, 0.f, 0.f};
     float wlo[3], whi[3];
     widen_box(tlo, thi, wlo, whi);
@@ -1856,8 +1884,14 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points_tc(PointsArgs a) {
                     bf = -2.f * (tig == 0 ? y.x : (tig == 1 ? y.y : y.z));
                 }
                 float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-                cross_mma<PREC>(d0, feat[0], feat[1], bf);   // rows g, g+8
-                cross_mma<PREC>(d1, feat[2], feat[3], bf);   // rows g+16, g+24
+                if (PREC == SF_PREC_BF16) {
+                    const uint32_t b16 = bf16_pair_from_tf32_layout(bf);
+                    mma_bf16(d0, fa16[0], fa16[1], b16);     // rows g, g+8
+                    mma_bf16(d1, fa16[2], fa16[3], b16);     // rows g+16, g+24
+                } else {
+                    cross_mma<PREC>(d0, feat[0], feat[1], bf);   // rows g, g+8
+                    cross_mma<PREC>(d1, feat[2], feat[3], bf);   // rows g+16, g+24
+                }
                 // epilogue: columns 2 tig, 2 tig + 1 of this n-tile
 #pragma unroll
                 for (int cc = 0; cc < 2; ++cc) {
@@ -1910,6 +1944,9 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points_tc(PointsArgs a) {
 template <int KER, bool CLIP>
 static cudaError_t launch_points_tc(int prec, const PointsArgs &a, int64_t nleaf, cudaStream_t s) {
     KTimer t("k_points_tc", s);
+    if (prec == SF_PREC_BF16)
+        return launch(k_points_tc<KER, CLIP, SF_PREC_BF16>, dim3(blocks_for(nleaf, kPtWarps)),
+                      dim3(kPtWarps * 32), 0, s, a);
     if (prec == SF_PREC_3XTF32)
         return launch(k_points_tc<KER, CLIP, SF_PREC_3XTF32>, dim3(blocks_for(nleaf, kPtWarps)),
                       dim3(kPtWarps * 32), 0, s, a);

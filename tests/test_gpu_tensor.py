@@ -1,6 +1,6 @@
-"""Tensor-core cross-term precision variants of the point densities (TF32 and
-3xTF32) against the FP64 oracle: the measured error of every result, against
-the a priori bounds stated in include/scalefree.h."""
+"""Tensor-core cross-term precision variants of the point densities (TF32,
+3xTF32 and BF16) against the FP64 oracle: the measured error of every result,
+against the a priori bounds stated in include/scalefree.h."""
 import json
 import os
 
@@ -18,10 +18,16 @@ pytestmark = pytest.mark.gpu
 # |dq| <~ 2^-10 * 2 |x||y| / h^2 with |x| <~ e (half the query group's extent) and
 # |y| <~ e + 3h: about 1e-2 for e ~ h; the Gaussian's relative error is |dq|/2, the
 # Epanechnikov's |dq|/(1 - q), larger near the edge. 3xTF32 leaves 2^-21 instead
-# of 2^-10. Measured on this cloud (GB300): Gaussian 4.4e-2 (TF32) and 1.6e-5
-# (3xTF32); Epanechnikov 1.5e-1 and 8.8e-5; FP32 below 3e-7 for both.
-BOUNDS = {"tf32": {1: 1e-1, 0: 3e-1}, "3xtf32": {1: 5e-5, 0: 2e-4}, "fp32": {1: 1e-5, 0: 1e-5}}
-BANDS = {"tf32": 2e-2, "3xtf32": 2e-5, "fp32": 1e-6}     # cutoff ambiguity band
+# of 2^-10, BF16 (8 significant bits) 2^-8: eight times TF32's. The Epanechnikov
+# relative error has no bound near the support edge (1 - q -> 0), so its BF16 bound
+# is loose; the rms error is the useful figure there. Measured on this cloud
+# (GB300), max / rms: Gaussian TF32 4.4e-2 / 1.0e-3, 3xTF32 1.6e-5 / 9.5e-7,
+# BF16 6.5e-1 / 1.1e-2; Epanechnikov TF32 1.5e-1 / 6.7e-3, 3xTF32 8.8e-5 / 4.3e-6,
+# BF16 3.0 / 5.3e-2; FP32 below 3e-7 for both.
+BOUNDS = {"tf32": {1: 1e-1, 0: 3e-1}, "3xtf32": {1: 5e-5, 0: 2e-4}, "fp32": {1: 1e-5, 0: 1e-5},
+          "bf16": {1: 1.0, 0: 6.0}}
+RMS_BOUNDS = {"tf32": 2e-2, "3xtf32": 2e-5, "fp32": 1e-6, "bf16": 1.6e-1}
+BANDS = {"tf32": 2e-2, "3xtf32": 2e-5, "fp32": 1e-6, "bf16": 1.6e-1}     # cutoff ambiguity band
 
 
 @pytest.mark.parametrize("kernel", [oracle.GAUSS3, oracle.EPAN])
@@ -41,7 +47,7 @@ def test_tensor_core_point_densities_error(kernel):
         h, _, _ = oracle.knn(xyz, 32)
         inb = np.nonzero(oracle.in_box(xyz, roi))[0]
         for name, prec in (("fp32", L.SF_PREC_FP32), ("tf32", L.SF_PREC_TF32),
-                           ("3xtf32", L.SF_PREC_3XTF32)):
+                           ("3xtf32", L.SF_PREC_3XTF32), ("bf16", L.SF_PREC_BF16)):
             p = L.make_params(rule=L.SF_BW_KNN, k=32)
             p.prec = prec
             if name == "fp32":
@@ -65,7 +71,9 @@ def test_tensor_core_point_densities_error(kernel):
                 f.write(json.dumps({"kernel": int(kernel), **report}) + "\n")
         for name, rep in report.items():
             assert rep["max_rel"] <= BOUNDS[name][int(kernel)], (name, rep)
+            assert rep["rms_rel"] <= RMS_BOUNDS[name], (name, rep)
         assert report["3xtf32"]["max_rel"] < report["tf32"]["max_rel"]
+        assert report["tf32"]["rms_rel"] < report["bf16"]["rms_rel"]
     finally:
         L.sf_free_index(idx)
 
