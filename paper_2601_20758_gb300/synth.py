@@ -13,6 +13,8 @@ reach:
                        radius ratio lambda), points at the deepest centres
 * ``cosmology_cloud``  80% Soneira-Peebles + 20% uniform background in a
                        periodic unit box (coordinates wrapped into [0, 1))
+* ``large_cloud_device`` 80% Soneira-Peebles + 20% in 10,000 NFW halos, a
+                       billion points drawn on the GPU
 """
 from __future__ import annotations
 
@@ -148,3 +150,92 @@ def random_densities(n: int, seed: int) -> np.ndarray:
     """Positive float32 values spread over several decades (selection inputs)."""
     r = _rng(seed)
     return np.exp(r.normal(0.0, 3.0, n)).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Large clouds, drawn on the GPU (a billion points in seconds): same recipes,
+# PyTorch's counter-based (Philox) CUDA generator, fixed seeds.
+# ---------------------------------------------------------------------------
+def _ball_t(torch, g, m: int, device):
+    d = torch.randn((m, 3), generator=g, device=device, dtype=torch.float64)
+    d /= torch.linalg.vector_norm(d, dim=1, keepdim=True)
+    return d * torch.rand((m, 1), generator=g, device=device, dtype=torch.float64).pow(1.0 / 3.0)
+
+
+def _nfw_mass(torch, x):
+    """NFW enclosed-mass profile m(x) = ln(1 + x) - x / (1 + x)."""
+    return torch.log1p(x) - x / (1.0 + x)
+
+
+def large_cloud_device(n: int = 1 << 30, seed: int = SEED_BASE + 3, halos: int = 10_000,
+                       halo_fraction: float = 0.2, device: str = "cuda"):
+    """Soneira-Peebles clustering (eta = 4, lambda = 1.9, 12 levels, top radius 0.25)
+    plus `halos` NFW halos holding `halo_fraction` of the points, on the device.
+
+    Halos: concentration c ~ U[5, 15]; mass log-uniform over three decades; point
+    count proportional to mass; virial radius proportional to M^(1/3), the largest
+    0.02; centres uniform in the unit cube; radii by inverting m(x) / m(c) = u on
+    [0, c] (bisection), r = x r_vir / c; isotropic directions. Coordinates wrapped
+    into [0, 1) as float32. Returns (xyz [n, 3] float32 on the device, centre of
+    the most massive halo as float64 numpy).
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = torch.float64
+    n_halo = int(round(halo_fraction * n))
+    n_sp = n - n_halo
+    # Soneira-Peebles: level by level, every sphere spawns eta sub-spheres
+    eta, lam, levels, radius = 4, 1.9, 12, 0.25
+    per_top = eta ** (levels - 1)
+    n_top = max(1, -(-n_sp // per_top))
+    c = torch.rand((n_top, 3), generator=g, device=device, dtype=f64)
+    rad = radius
+    for _lvl in range(1, levels):
+        c = c.repeat_interleave(eta, dim=0) + rad * _ball_t(torch, g, c.shape[0] * eta, device)
+        rad = rad / lam
+    if c.shape[0] > n_sp:
+        keep = torch.randperm(c.shape[0], generator=g, device=device)[:n_sp]
+        c = c[torch.sort(keep).values]
+    # NFW halos
+    mass = torch.exp(torch.rand(halos, generator=g, device=device, dtype=f64) * float(np.log(1000.0)))
+    conc = 5.0 + 10.0 * torch.rand(halos, generator=g, device=device, dtype=f64)
+    rvir = 0.02 * (mass / mass.max()).pow(1.0 / 3.0)
+    centre = torch.rand((halos, 3), generator=g, device=device, dtype=f64)
+    counts = torch.floor(mass / mass.sum() * n_halo).long()
+    counts[torch.argmax(mass)] += n_halo - int(counts.sum())
+    hid = torch.repeat_interleave(torch.arange(halos, device=device), counts)
+    u = torch.rand(n_halo, generator=g, device=device, dtype=f64)
+    ch = conc[hid]
+    target = u * _nfw_mass(torch, ch)
+    lo = torch.zeros_like(ch)
+    hi = ch.clone()
+    for _ in range(48):  # bisection for m(x) = target on [0, c]
+        mid = 0.5 * (lo + hi)
+        below = _nfw_mass(torch, mid) < target
+        lo = torch.where(below, mid, lo)
+        hi = torch.where(below, hi, mid)
+    r = 0.5 * (lo + hi) * rvir[hid] / ch
+    d = torch.randn((n_halo, 3), generator=g, device=device, dtype=f64)
+    d /= torch.linalg.vector_norm(d, dim=1, keepdim=True)
+    pts = torch.cat([c, centre[hid] + r[:, None] * d])
+    del c, d, r, u, ch, target, lo, hi, hid
+    pts = pts[torch.randperm(n, generator=g, device=device)]
+    pts = pts - torch.floor(pts)
+    xyz = pts.to(torch.float32)
+    del pts
+    xyz[xyz >= 1.0] = 0.0
+    big = int(torch.argmax(mass))
+    return xyz.contiguous(), centre[big].cpu().numpy()
+
+
+def zoom_rois(centre, n_roi: int = 8, decades: float = 3.0):
+    """Cubic ROIs of edge 10^(-decades * i / (n_roi - 1)), i = 0..n_roi-1, centred on
+    ``centre`` and shifted to stay inside the unit cube."""
+    c = np.asarray(centre, dtype=np.float64)
+    rois = []
+    for i in range(n_roi):
+        e = 10.0 ** (-decades * i / (n_roi - 1))
+        lo = np.clip(c - e / 2, 0.0, 1.0 - e)
+        rois.append((lo.copy(), lo + e))
+    return rois
