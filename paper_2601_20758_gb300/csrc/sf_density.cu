@@ -623,6 +623,7 @@ struct MrArgs {
 
 constexpr int kWalkWarps = 8;
 constexpr int kWX = 8, kWY = 4;  // node tile of one warp in the split pipeline (x, y)
+constexpr int kLaneTables = 10;   // staged points from which each lane fills its own tables
 
 struct WalkWarpSmem {
     int stack[kStack];
@@ -829,8 +830,44 @@ __global__ void __launch_bounds__(kGridThreads, 4)
             }
             __syncwarp();
             // ---- per-axis tables over the whole tile: factors inside the footprint,
-            // "no support" values outside it (so the accumulation needs no range tests)
+            // "no support" values outside it (so the accumulation needs no range tests).
+            // Many staged points: each staging lane fills its own point's entries;
+            // few: the entries are spread over all lanes. Both give the same values.
             constexpr int kEnt = kWX + kWY + TZ;
+            auto entry = [&](int axis, int ii, bool inside, float pc, float u, float c, float2 nc) {
+                const float d = (nc.x - pc) + nc.y;
+                const float t = d * u;
+                const float q = t * t;
+                const bool sup = inside && q < KDef<KER>::qmax;
+                if (KER == SF_K_GAUSS3) {
+                    const float w = sup ? ex2_approx(-q) : 0.f;
+                    if (axis == 0) return make_float2(w * c, sup ? q : kBig);
+                    if (axis == 1) return make_float2(w, sup ? q : kBig);
+                    return make_float2(w, sup ? KDef<KER>::qmax - q : -1.f);
+                }
+                if (axis < 2) return make_float2(sup ? q : kBig, 0.f);
+                return make_float2(sup ? c * (1.0f - q) : -kBig, 0.f);
+            };
+            if (ns >= kLaneTables) {
+                if (acc_pt) {
+                    const int s = __popc(bal & ((1u << lane) - 1u));
+                    const float c = E.cnorm * ((rl[0] * rl[1]) * rl[2]);
+                    const float u0 = KDef<KER>::uscale * rl[0], u1 = KDef<KER>::uscale * rl[1],
+                                u2 = KDef<KER>::uscale * rl[2];
+                    const int x0 = fp.x & 255, x1 = (fp.x >> 8) & 255;
+                    const int y0 = (fp.x >> 16) & 255, y1 = (fp.x >> 24) & 255;
+                    const int z0 = fp.y & 255, z1 = (fp.y >> 8) & 255;
+#pragma unroll
+                    for (int i = 0; i < kWX; ++i)
+                        S.tx[s][i] = entry(0, i, i >= x0 && i <= x1, p.x, u0, c, S.axt[i]);
+#pragma unroll
+                    for (int i = 0; i < kWY; ++i)
+                        S.ty[s][i] = entry(1, i, i >= y0 && i <= y1, p.y, u1, c, S.axt[kWX + i]);
+#pragma unroll
+                    for (int i = 0; i < TZ; ++i)
+                        S.tz[s][i] = entry(2, i, i >= z0 && i <= z1, p.z, u2, c, S.axt[kWX + kWY + i]);
+                }
+            } else
             for (int e = lane; e < ns * kEnt; e += 32) {
                 const int s = e / kEnt;
                 const int j = e - s * kEnt;
@@ -848,21 +885,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                 const float4 U = S.su[s];
                 const float pc = axis == 0 ? P.x : (axis == 1 ? P.y : P.z);
                 const float u = axis == 0 ? U.x : (axis == 1 ? U.y : U.z);
-                const float2 nc = S.axt[j];
-                const float d = (nc.x - pc) + nc.y;
-                const float t = d * u;
-                const float q = t * t;
-                const bool sup = inside && q < KDef<KER>::qmax;
-                float2 v;
-                if (KER == SF_K_GAUSS3) {
-                    const float w = sup ? ex2_approx(-q) : 0.f;
-                    if (axis == 0) v = make_float2(w * P.w, sup ? q : kBig);
-                    else if (axis == 1) v = make_float2(w, sup ? q : kBig);
-                    else v = make_float2(w, sup ? KDef<KER>::qmax - q : -1.f);
-                } else {
-                    if (axis < 2) v = make_float2(sup ? q : kBig, 0.f);
-                    else v = make_float2(sup ? P.w * (1.0f - q) : -kBig, 0.f);
-                }
+                const float2 v = entry(axis, ii, inside, pc, u, P.w, S.axt[j]);
                 if (axis == 0) S.tx[s][ii] = v;
                 else if (axis == 1) S.ty[s][ii] = v;
                 else S.tz[s][ii] = v;
