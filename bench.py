@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-prec", action="store_true",
                     help="skip the tensor-core precision variants of the point densities")
     ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-slots", type=int, default=4, help="concurrent requests (streams)")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the pair-counting pass (value and roofline become null)")
     return ap.parse_args()
@@ -549,7 +550,7 @@ def load_traffic(kernel):
 def run_serving(args, L, torch, d_xyz, p, rois):
     """Continuous admission of ROI recomputes (grid + point densities + selection)
     arriving as a Poisson stream (mean 200/s) that walks zoom and pan over three
-    decades of scale with grid edges 64..256, on 4 slots (streams)."""
+    decades of scale with grid edges 64..256, on --serve-slots slots (streams)."""
     from paper_2601_20758_gb300 import serve
     n = d_xyz.shape[0]
     idx = L.sf_build_index(d_xyz)
@@ -559,7 +560,7 @@ def run_serving(args, L, torch, d_xyz, p, rois):
         reqs = serve.navigation_requests(args.serve_requests, rate=200.0, centre=centre, seed=2601,
                                          select_every=10)
         free, _ = torch.cuda.mem_get_info()
-        slots = 4
+        slots = args.serve_slots
         ex = serve.GpuExecutor(idx, p, L.SF_K_GAUSS3, n, slots=slots, max_nodes=256 ** 3)
         srv = serve.Server(ex, slots=slots, mem_budget=int(0.5 * free), n_points=n)
         try:
