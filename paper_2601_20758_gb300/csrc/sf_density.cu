@@ -675,6 +675,14 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_mr_walk(MrArgs a, uint32_t 
     if (!EMIT && lane == 0) cnt[gt] = total;
 }
 
+__global__ void k_total64(const uint32_t *__restrict__ cnt, int n, unsigned long long *out) {
+    unsigned long long t = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) t += cnt[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(out, t);
+}
+
 __global__ void k_grid_item_counts(const uint32_t *__restrict__ cnt, int ntiles, uint32_t lpw,
                                    uint32_t *__restrict__ ic) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1043,14 +1051,25 @@ static cudaError_t dispatch_grid(int bw, bool clip, const GridArgs &a, unsigned 
 // ---- split pipeline ---------------------------------------------------------
 // Sizing: count candidate leaves of every (ROI, tile); returns the total (syncs).
 template <int KER, int BW, bool CLIP, int TZ>
+// tot: 16 bytes -- [0] the 32-bit scan total, [1] the item count of mr_exec,
+// bytes 8..15 the same total summed in 64 bits (guards the 32-bit offsets).
 static sf_status mr_count(const MrArgs &a, uint32_t *cnt, uint32_t *off, uint32_t *tot,
                           uint32_t *h_total, cudaStream_t s) {
     const unsigned wb = blocks_for(a.ntiles, kWalkWarps);
     SF_TRY_CUDA(launch(k_mr_walk<KER, BW, CLIP, false, TZ>, dim3(wb), dim3(kWalkWarps * 32), 0, s, a,
                        cnt, (const uint32_t *)nullptr, (int *)nullptr));
     SF_TRY(scan_u32(cnt, off, a.ntiles, tot, s));
-    SF_TRY_CUDA(cudaMemcpyAsync(h_total, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    unsigned long long *tot64 = reinterpret_cast<unsigned long long *>(tot + 2);
+    SF_TRY_CUDA(cudaMemsetAsync(tot64, 0, sizeof(unsigned long long), s));
+    SF_TRY_CUDA(launch(k_total64, dim3(std::min(blocks_for(a.ntiles, 256), 152u * 4u)), dim3(256), 0, s,
+                       (const uint32_t *)cnt, a.ntiles, tot64));
+    unsigned long long h64 = 0;
+    SF_TRY_CUDA(cudaMemcpyAsync(&h64, tot64, sizeof h64, cudaMemcpyDeviceToHost, s));
     SF_TRY_CUDA(cudaStreamSynchronize(s));
+    if (h64 > 0x7fffffffull)
+        return fail(SF_ERR_CAPACITY, "grid candidate lists of %llu entries exceed 2^31; use fewer nodes or a smaller ROI",
+                    h64);
+    *h_total = (uint32_t)h64;
     return SF_OK;
 }
 
@@ -1151,7 +1170,7 @@ static sf_status mr_once(const MrArgs &a, int items_per_slot, cudaStream_t s) {
     MrBuffers b;
     b.cnt = sc.get<uint32_t>(a.ntiles);
     b.off = sc.get<uint32_t>(a.ntiles);
-    b.tot = sc.get<uint32_t>(2);
+    b.tot = sc.get<uint32_t>(4);
     SF_TRY_SCRATCH(sc);
     uint32_t total = 0;
     SF_TRY((mr_count<KER, BW, CLIP, TZ>(a, b.cnt, b.off, b.tot, &total, s)));
@@ -1418,7 +1437,7 @@ sf_status batch_create(sf_index *idx, int nroi, const sf_box *rois, const GridSp
         (e = cudaMalloc(&p_mass, sizeof(double) * 2 * nroi)) != cudaSuccess ||
         (e = cudaMalloc(&p_cnt, sizeof(uint32_t) * ntiles)) != cudaSuccess ||
         (e = cudaMalloc(&p_off, sizeof(uint32_t) * ntiles)) != cudaSuccess ||
-        (e = cudaMalloc(&p_tot, sizeof(uint32_t) * 2)) != cudaSuccess) {
+        (e = cudaMalloc(&p_tot, sizeof(uint32_t) * 4)) != cudaSuccess) {
         for (void *q : {p_axis, p_rois, p_tr, p_mp, p_mass, p_cnt, p_off, p_tot})
             if (q) cudaFree(q);
         return bail(fail(SF_ERR_OOM, "batch plan: %s", cudaGetErrorString(e)));
