@@ -21,7 +21,7 @@ as plain definitions in double precision over all pairs:
 * ``mbe``             pilot -> aveDen -> l_k^(j) -> final grid    (Eqs. 2, 5, 6, 7)
 * ``select``          threshold selection of points by density   (Sec. 4.1)
 
-Readings where the paper is silent or ambiguous (each is listed in the design doc):
+Readings where the paper is silent or ambiguous:
 closed box membership; vertex-centred nodes s_k = (hi-lo)/(res_k-1); natural
 log in Eq. 1; numpy-"linear" percentiles; Eq. 5 read as the arithmetic mean
 (the text and Algorithm 3 divide by the count); l^(j) = 5 s_k where the pilot
