@@ -54,6 +54,7 @@ struct KnnArgs {
     float *h_sorted;          // out: h per sorted point
     uint32_t *nbr_orig;       // out (nullable): [n][k] by original index
     int *leaf_list;           // [slots][kLeafList] accepted leaves of the current query leaf
+    uint32_t *leaf_mask;      // [slots][kLeafList] their points inside the warp envelope
     double *band_d;           // [slots][kBand][32] band members' FP64 d2
     uint32_t *band_i;         // [slots][kBand][32] band members' original ids
     unsigned int *next_leaf;  // work counter (zeroed before launch)
@@ -81,15 +82,16 @@ struct KnnWarp {
     const TreeView &tv;
     const uint32_t *perm;
     KnnWarpSmem &S;
-    int *leaf_list;  // this warp's recorded leaves
+    int *leaf_list;        // this warp's recorded leaves
+    uint32_t *leaf_mask;   // and, per leaf, its points inside the envelope
     float4 q;
     float r2;
     float env_lo[3], env_hi[3];  // warp envelope of all balls
     int nlist;
     bool overflow;
 
-    __device__ KnnWarp(const TreeView &t, const uint32_t *p, KnnWarpSmem &s, int *c)
-        : tv(t), perm(p), S(s), leaf_list(c) {}
+    __device__ KnnWarp(const TreeView &t, const uint32_t *p, KnnWarpSmem &s, int *c, uint32_t *cm)
+        : tv(t), perm(p), S(s), leaf_list(c), leaf_mask(cm) {}
 
     // Mask of the children (lane c holds child c at level cl) within the ball
     // of at least one lane. Conservative: relative slack 1e-5.
@@ -170,7 +172,7 @@ struct KnnWarp {
     // at a time (the next leaf's points load while the current one is used):
     // chunk(n) is called with S.pts[0..n) staged (x, y, z, original id bits).
     template <typename Chunk>
-    __device__ __forceinline__ void visit(int nl, Chunk chunk) {
+    __device__ __forceinline__ void visit(int nl, Chunk chunk, int record = -1) {
         const int lane = threadIdx.x & 31;
         float4 pn = make_float4(0.f, 0.f, 0.f, 0.f);
         uint32_t idn = 0;
@@ -191,6 +193,7 @@ struct KnnWarp {
                             p.y <= env_hi[1] && p.z >= env_lo[2] && p.z <= env_hi[2];
             const unsigned m = __ballot_sync(0xffffffffu, in);
             if (in) S.pts[__popc(m & ((1u << lane) - 1u))] = p;
+            if (record >= 0 && lane == 0 && record + li < kLeafList) leaf_mask[record + li] = m;
             __syncwarp();
             chunk(__popc(m));
             __syncwarp();
@@ -231,8 +234,8 @@ struct KnnWarp {
             for (int i = lane; i < nl; i += 32)
                 if (nlist + i < kLeafList) leaf_list[nlist + i] = S.cand[i];
             if (nlist + nl > kLeafList) overflow = true;
+            visit(nl, fn, nlist);
             nlist += nl;
-            visit(nl, fn);
             nl = 0;
         }
         __syncwarp();
@@ -264,16 +267,51 @@ struct KnnWarp {
         }
         walk_points(per_chunk);
     }
+
+    // As each(), but a recorded leaf is loaded only if some lane needs its points:
+    // cls(lo, hi) classifies the leaf box for this lane (0: visit, 1: every point
+    // counts as below, 2: nothing to do) and below(n) adds the n envelope points of
+    // a leaf classified 1 (the lane's own point excluded).
+    template <typename Fn, typename Cls, typename Below>
+    __device__ __forceinline__ void each_pruned(Fn fn, Cls cls, Below below, int64_t self_leaf) {
+        const int lane = threadIdx.x & 31;
+        if (overflow) {
+            each(fn);
+            return;
+        }
+        auto per_chunk = [&](int n) {
+            for (int t = 0; t < n; ++t) fn(S.pts[t]);
+        };
+        for (int base = 0; base < nlist; base += 32) {
+            const int nb = min(32, nlist - base);
+            const int lidx = lane < nb ? leaf_list[base + lane] : 0;
+            const uint32_t lmask = lane < nb ? leaf_mask[base + lane] : 0u;
+            for (int t = 0; t < nb; ++t) {
+                const int L = __shfl_sync(0xffffffffu, lidx, t);
+                const uint32_t m = __shfl_sync(0xffffffffu, lmask, t);
+                const float4 lo = __ldg(&tv.nlo[tv.off[0] + L]), hi = __ldg(&tv.nhi[tv.off[0] + L]);
+                const int c = cls(lo, hi);
+                if (!__any_sync(0xffffffffu, c == 0)) {
+                    if (c == 1) below(__popc(m) - ((L == self_leaf && ((m >> lane) & 1u)) ? 1 : 0));
+                    continue;
+                }
+                __syncwarp();
+                if (lane == 0) S.cand[0] = L;
+                __syncwarp();
+                visit(1, per_chunk);
+            }
+        }
+    }
 };
 
-__device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, double *bd, uint32_t *bi,
+__device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, uint32_t *leaf_mask, double *bd, uint32_t *bi,
                          int64_t leaf) {
     const int lane = threadIdx.x & 31;
     const TreeView &tv = a.tv;
     const int k = a.k;
     const int64_t qi = leaf * kLeaf + lane;
     const bool valid = qi < tv.n;
-    KnnWarp W(tv, a.perm, S, leaf_list);
+    KnnWarp W(tv, a.perm, S, leaf_list, leaf_mask);
     W.q = valid ? __ldg(&tv.pos[qi]) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 q = W.q;
     const uint32_t qid = valid ? __ldg(&a.perm[qi]) : 0u;
@@ -420,7 +458,28 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, doubl
         const float sub_w = e_hi - e_lo;
         const float sub_inv = sub_w > 0.f ? (float)kNB / sub_w : 0.f;
         int nbelow = 0, nband = 0, below_next = 0;
-        W.each([&](float4 p) {
+        // leaves wholly below this lane's band (by the far corner of their box) or
+        // wholly above it (by the near corner) need no point loads; the margins
+        // cover the rounding of the FP32 distances
+        auto cls = [&](float4 lo, float4 hi) -> int {
+            if (!act) return 2;
+            const float gx = fmaxf(fmaxf(lo.x - q.x, q.x - hi.x), 0.f);
+            const float gy = fmaxf(fmaxf(lo.y - q.y, q.y - hi.y), 0.f);
+            const float gz = fmaxf(fmaxf(lo.z - q.z, q.z - hi.z), 0.f);
+            const float fx = fmaxf(fabsf(q.x - lo.x), fabsf(q.x - hi.x));
+            const float fy = fmaxf(fabsf(q.y - lo.y), fabsf(q.y - hi.y));
+            const float fz = fmaxf(fabsf(q.z - lo.z), fabsf(q.z - hi.z));
+            const float dmin = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+            const float dmax = fmaf(fz, fz, fmaf(fy, fy, fx * fx));
+            if (dmax * (1.0f + 1.0e-5f) < band_lo) return 1;
+            if (dmin * (1.0f - 1.0e-5f) > band_hi) return 2;
+            return 0;
+        };
+        auto below_all = [&](int n) {
+            nbelow += n;
+            below_next += n;
+        };
+        W.each_pruned([&](float4 p) {
             const float d = d2_f32(q, p);
             if (d <= bhi_a) {
                 const uint32_t id = __float_as_uint(p.w);
@@ -438,7 +497,7 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, doubl
                     else if (d <= e_hi) S.hist[min(kNB - 1, (int)((d - e_lo) * sub_inv))][lane] += 1;
                 }
             }
-        });
+        }, cls, below_all, leaf);
         __syncwarp();
         if (act) {
             need = k - nbelow;
@@ -529,6 +588,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32, 7) k_knn(KnnArgs a) {
     KnnWarpSmem &S = reinterpret_cast<KnnWarpSmem *>(smem_raw)[warp];
     const int64_t slot = (int64_t)blockIdx.x * kKnnWarps + warp;
     int *leaf_list = a.leaf_list + slot * kLeafList;
+    uint32_t *leaf_mask = a.leaf_mask + slot * kLeafList;
     double *bd = a.band_d + slot * (kBand * 32);
     uint32_t *bi = a.band_i + slot * (kBand * 32);
     const int64_t nleaf = a.tv.cnt[0];
@@ -537,7 +597,7 @@ __global__ void __launch_bounds__(kKnnWarps * 32, 7) k_knn(KnnArgs a) {
         if ((threadIdx.x & 31) == 0) leaf = atomicAdd(a.next_leaf, 1u);
         leaf = __shfl_sync(0xffffffffu, leaf, 0);
         if ((int64_t)leaf >= nleaf) break;
-        knn_leaf(a, S, leaf_list, bd, bi, (int64_t)leaf);
+        knn_leaf(a, S, leaf_list, leaf_mask, bd, bi, (int64_t)leaf);
     }
 }
 
@@ -584,6 +644,7 @@ sf_status knn_run(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_sorted,
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, need_blocks));
     Scratch sc(s);
     a.leaf_list = sc.get<int>(blocks * kKnnWarps * (int64_t)kLeafList);
+    a.leaf_mask = sc.get<uint32_t>(blocks * kKnnWarps * (int64_t)kLeafList);
     a.band_d = sc.get<double>(blocks * kKnnWarps * (int64_t)kBand * 32);
     a.band_i = sc.get<uint32_t>(blocks * kKnnWarps * (int64_t)kBand * 32);
     a.next_leaf = sc.get<unsigned int>(1);
