@@ -20,7 +20,9 @@
 //  4. band pass: points clearly below the bin are in; the ones whose FP32 d2
 //     lies in the bin (widened by a relative 2e-6) are re-evaluated in FP64 (no
 //     FMA contraction) into a per-lane buffer of 64 in global memory and ranked
-//     by (d2, original index) -- one pass resolves almost every lane. If a band
+//     by (d2, original index) -- one pass resolves almost every lane; recorded
+//     leaves whose box lies wholly below or above every lane's band are counted
+//     from their envelope masks instead of being reloaded. If a band
 //     overflows its buffer the bin is split again (the band pass has already
 //     binned the bracket for that round); at FP32 resolution (exact duplicates)
 //     the remaining members are extracted one by one.
