@@ -276,6 +276,33 @@ def test_mbe_points_interp(L):
         L.sf_free_index(idx)
 
 
+@pytest.mark.parametrize("kernel", [oracle.EPAN, oracle.GAUSS3])
+def test_mbe_points_direct(L, kernel):
+    """The paper's estimator at the points themselves (per-point anisotropic smoothing
+    lengths, clip scope): the DIRECT point path with its third bandwidth mode."""
+    xyz = synth.plain_cloud(8000, seed=15)
+    roi = ((0.1, 0.2, 0.1), (0.8, 0.9, 0.85))
+    dims = (24, 20, 28)
+    idx, d = _index(L, xyz)
+    try:
+        p = L.make_params(rule=L.SF_BW_MBE, scope=L.SF_SCOPE_CLIP)
+        n = xyz.shape[0]
+        dens = torch.empty(n, device="cuda")
+        ids = torch.empty(n, dtype=torch.int32, device="cuda")
+        cnt = L.sf_kde_points(idx, L.make_box(*roi), dims, kernel, p, dens, ids)
+        ref = oracle.mbe(xyz, roi, dims, kernel=kernel)
+        inb = np.nonzero(ref["member"])[0]
+        assert cnt == inb.size
+        got_ids = ids[:cnt].cpu().numpy().view(np.uint32).astype(np.int64)
+        assert np.array_equal(np.sort(got_ids), inb)
+        order = np.argsort(got_ids)
+        pref = oracle.density_at(xyz, ref["ell_j"], xyz[inb].astype(np.float64), kernel,
+                                 1.0 / ref["nb"], member=ref["member"])
+        density_check(dens[:cnt].cpu().numpy()[order], pref, label="mbe points direct")
+    finally:
+        L.sf_free_index(idx)
+
+
 def test_mbe_degenerate(L):
     xyz = synth.uniform_cloud(1000, seed=3)
     idx, d = _index(L, xyz)
