@@ -185,7 +185,46 @@ POINT_CASES = [
     ("epan_knn_global", "plain", "knn", oracle.EPAN, "global", ((0, 0, 0), (1, 1, 1)), 16),
     ("epan_fixed_clip", "plain", "fixed", oracle.EPAN, "clip", ((0.2, 0.1, 0.3), (0.8, 0.9, 0.7)), (0.05, 0.07, 0.04)),
     ("gauss_knn_cluster", "cluster", "knn", oracle.GAUSS3, "global", ((0.3, 0.3, 0.3), (0.7, 0.7, 0.7)), 64),
+    ("gauss_knn_clip", "cluster", "knn", oracle.GAUSS3, "clip", ((0.25, 0.3, 0.2), (0.75, 0.7, 0.8)), 32),
 ]
+
+
+@pytest.mark.parametrize("kernel", [oracle.GAUSS3, oracle.EPAN])
+def test_count_support_pairs(L, kernel):
+    """The benchmark's work unit: in-support (node, particle) and (point, particle)
+    pairs counted by the kernels' counting variants against the oracle's count. They
+    can differ only by pairs whose q sits on the cutoff within rounding -- for the
+    Epanechnikov kernel every particle's k-th neighbour lies at q = 1 exactly -- so
+    the GPU count must lie between the oracle's counts with the cutoff moved by a
+    relative 2e-6 either way (smoothing lengths scaled by sqrt(1 -+ 2e-6))."""
+    import ctypes
+    xyz = synth.plain_cloud(20000, seed=9)
+    n = xyz.shape[0]
+    roi = ((0.1, 0.15, 0.1), (0.9, 0.85, 0.9))
+    dims = (24, 20, 28)
+    idx, d = _index(L, xyz)
+    try:
+        p = L.make_params(rule=L.SF_BW_KNN, k=32)
+        L.sf_bandwidths(idx, p)
+        gp, pp = ctypes.c_int64(0), ctypes.c_int64(0)
+        box = L.make_box(*roi)
+        L._check("sf_count_support_pairs", L.load().sf_count_support_pairs(
+            idx, ctypes.byref(box), (ctypes.c_int32 * 3)(*dims), kernel, ctypes.byref(p),
+            ctypes.byref(gp), ctypes.byref(pp), None))
+        h_ref, _, _ = oracle.knn(xyz, 32)
+        ell = oracle.iso_ell(h_ref)
+        inb = oracle.in_box(xyz, roi)
+        counts = []
+        for f in (np.sqrt(1.0 - 2e-6), np.sqrt(1.0 + 2e-6)):
+            rg = oracle.kde_grid(xyz, ell * f, roi, dims, kernel, oracle.SCOPE_GLOBAL)
+            rp = oracle.density_at(xyz, ell * f, xyz[inb].astype(np.float64), kernel, 1.0 / n)
+            counts.append((int(rg["pairs"].sum()), int(rp["pairs"].sum())))
+        (g_lo, p_lo), (g_hi, p_hi) = counts
+        assert g_lo > 0 and p_lo > 0
+        assert g_lo <= gp.value <= g_hi, (g_lo, gp.value, g_hi)
+        assert p_lo <= pp.value <= p_hi, (p_lo, pp.value, p_hi)
+    finally:
+        L.sf_free_index(idx)
 
 
 @pytest.mark.parametrize("case", POINT_CASES, ids=[c[0] for c in POINT_CASES])
