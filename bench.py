@@ -105,28 +105,34 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.out = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
+        self.out = open(self.path, "w")
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
     def stop(self):
         if self.proc is None:
+            self.out.close()
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        self.out.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -323,7 +329,10 @@ def main():
     # ---- roofline of the dominant kernel
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    peaks = {}
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as fh:
+            peaks = json.load(fh)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak_tflops = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -534,12 +543,14 @@ def load_traffic(kernel):
     if not os.path.exists(path):
         return None
     try:
-        t = json.load(open(path))
+        with open(path) as fh:
+            t = json.load(fh)
         ent = t.get(kernel)
         if not ent:
             return None
         src = os.path.join(ROOT, "paper_2601_20758_gb300", "csrc", ent["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        with open(src, "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()[:16]
         if h != ent.get("source_sha256_16"):
             return None
         return ent["dram_bytes_per_launch"]
