@@ -48,7 +48,7 @@ typedef enum {
     SF_ERR_DEGENERATE = 5,  /* N <= k, fewer than 2 particles in B, P80 == P20     */
     SF_ERR_EMPTY_ROI = 6,   /* no particle of the scope lies in the ROI              */
     SF_ERR_BUSY = 7,        /* not admitted (serving)                                */
-    SF_ERR_CAPACITY = 8     /* an output buffer is smaller than the result           */
+    SF_ERR_CAPACITY = 8     /* an output buffer (or an internal list) is too small   */
 } sf_status;
 
 /* Kernels.
@@ -170,7 +170,8 @@ sf_status sf_knn_neighbours(sf_index *idx, int32_t k, uint32_t *d_nbr, float *d_
  * h_mass (nullable, host): FP64 total mass sum_n rho_n s_x s_y s_z; giving it
  * synchronises the stream.
  * Errors: INVALID_ARG, OOM, CUDA, DEGENERATE (MBE with N_B < 2 or P80 == P20),
- * EMPTY_ROI (scope CLIP and no point in B; d_out is zero-filled).
+ * EMPTY_ROI (scope CLIP and no point in B; d_out is zero-filled), CAPACITY (the
+ * per-tile candidate lists would exceed 2^31 entries: fewer nodes or a smaller ROI).
  * Device-side degenerate conditions are reported by the next call that
  * synchronises (h_mass given, or sf_sync_status).
  */
