@@ -31,7 +31,9 @@ excludes the point itself and breaks distance ties by the smaller index.
 
 Parity pins: see tests/test_oracle_pins.py (closed forms, invariants, brute
 force against a second, sort-based route, hand-derived golden values).
-The MBE pipeline end to end is "parity unpinned" beyond those pieces: the
+The MBE pipeline end to end is pinned only by invariants (exact power-of-two
+scale invariance, permutation invariance, the uniform-lattice interior, the
+zero-pilot cap): for its absolute values it is "parity unpinned", since the
 paper prints no density values for any input.
 """
 from __future__ import annotations

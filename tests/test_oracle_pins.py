@@ -281,6 +281,30 @@ def test_mbe_zero_pilot_gives_cap():
     assert np.all(ell_in[~zero] < 5 * out["s"])
 
 
+def test_mbe_scale_and_permutation_invariance():
+    """The whole estimator (Eqs. 1, 2, 5, 6, 7) under coordinates and box times 2^3: the
+    percentiles, l_k, s_k and l^(j) scale by 8 and every density by 2^-9, bit for bit
+    (powers of two scale exactly; ln N_B and aveDen / pDen are scale-free). Catches a
+    wrong power of l or s anywhere in the chain (a missing s_k in the cap, a square
+    instead of a cube root, a density not divided by the volume). Reordering the
+    particles changes the final densities only by summation order."""
+    xyz = synth.plain_cloud(3000, seed=12)
+    box = ((0.05, 0.1, 0.0), (0.95, 0.9, 1.0))
+    dims = (11, 9, 10)
+    box8 = tuple(tuple(8 * v for v in b) for b in box)
+    for kernel in (oracle.EPAN, oracle.GAUSS3):
+        a = oracle.mbe(xyz, box, dims, kernel=kernel)
+        b = oracle.mbe(xyz * np.float32(8), box8, dims, kernel=kernel)
+        assert np.array_equal(b["ell0"], a["ell0"] * 8)
+        assert np.array_equal(b["ell_j"], a["ell_j"] * 8)
+        assert np.array_equal(b["pilot"], a["pilot"] * 2.0 ** -9)
+        assert np.array_equal(b["final"]["rho"], a["final"]["rho"] * 2.0 ** -9)
+    perm = np.random.default_rng(4).permutation(xyz.shape[0])
+    c = oracle.mbe(xyz[perm], box, dims, kernel=oracle.EPAN)
+    a = oracle.mbe(xyz, box, dims, kernel=oracle.EPAN)
+    np.testing.assert_allclose(c["final"]["rho"], a["final"]["rho"], rtol=1e-12)
+
+
 def test_clip_scope_normalises_by_box_count():
     """CLIP scope: particles outside B are excluded and N_B normalises (Eq. 7 over B)."""
     xyz = np.array([[0.5, 0.5, 0.5], [0.5, 0.5, 0.55], [5, 5, 5]], dtype=np.float32)
