@@ -347,8 +347,9 @@ def main():
         roof = {"kernel": dom, "bound": "alu", "achieved": work / (avg_ms * 1e-3) / 1e12,
                 "peak": fp32_peak_tflops, "unit": "TFLOP/s"}
     else:
-        # sort / kNN: compulsory HBM bytes (read 12 B xyz, write 16 B point + 4 B index per point)
-        byts = n * 32
+        # kNN: compulsory bytes per point, 16 B read (the sorted point) + 4 B written (h);
+        # radix sort: 8 passes of 8-bit digits, each reading and writing 12 B per point
+        byts = n * 20 if dom == "k_knn" else n * 8 * 24
         roof = {"kernel": dom, "bound": "hbm", "achieved": byts / (avg_ms * 1e-3) / 1e9,
                 "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s"}
     if not pairs_step and roof["bound"] == "alu":
