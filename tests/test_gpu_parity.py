@@ -157,6 +157,41 @@ def test_grid_empty_clip_roi(L):
         L.sf_free_index(idx)
 
 
+@pytest.mark.parametrize("kernel", [oracle.EPAN, oracle.GAUSS3])
+def test_points_on_roi_faces_and_grid_nodes(L, kernel):
+    """A lattice whose planes are the ROI's faces and whose points sit exactly on grid
+    nodes (distance 0 pairs), plus duplicates of lattice points: closed-box membership,
+    clip scope, grid and point densities against the oracle."""
+    spacing = 1.0 / 16
+    lat = synth.lattice_cloud(17, spacing)                      # 0 .. 1 in steps of 1/16
+    extra = synth.uniform_cloud(1500, seed=31)
+    xyz = np.ascontiguousarray(np.concatenate([lat, extra, lat[::97]]))
+    roi = ((0.25, 0.25, 0.25), (0.75, 0.75, 0.75))              # faces on lattice planes
+    dims = (17, 17, 17)                                         # nodes every 1/32: on the lattice too
+    n = xyz.shape[0]
+    idx, d = _index(L, xyz)
+    try:
+        p = L.make_params(rule=L.SF_BW_KNN, k=12, scope=L.SF_SCOPE_CLIP)
+        L.sf_bandwidths(idx, p)
+        h_ref, _, _ = oracle.knn(xyz, 12)
+        ell = oracle.iso_ell(h_ref)
+        out = torch.empty(dims[0] * dims[1] * dims[2], device="cuda")
+        L.sf_kde_grid(idx, L.make_box(*roi), dims, kernel, p, out)
+        ref = oracle.kde_grid(xyz, ell, roi, dims, kernel, oracle.SCOPE_CLIP)
+        density_check(out.cpu().numpy(), ref, label="faces grid")
+        dens = torch.empty(n, device="cuda")
+        ids = torch.empty(n, dtype=torch.int32, device="cuda")
+        cnt = L.sf_kde_points(idx, L.make_box(*roi), None, kernel, p, dens, ids)
+        inb = oracle.in_box(xyz, roi)
+        assert cnt == int(inb.sum()) and cnt > 9 ** 3          # the 9^3 lattice points on or in B
+        order = np.argsort(ids[:cnt].cpu().numpy().view(np.uint32))
+        pref = oracle.density_at(xyz, ell, xyz[inb].astype(np.float64), kernel, 1.0 / int(inb.sum()),
+                                 member=inb)
+        density_check(dens[:cnt].cpu().numpy()[order], pref, label="faces points")
+    finally:
+        L.sf_free_index(idx)
+
+
 def test_grid_single_point_and_outside_roi(L):
     """One particle (a single leaf, the root itself); a ROI far from every particle."""
     xyz = np.array([[0.5, 0.5, 0.5]], dtype=np.float32)
