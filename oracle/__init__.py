@@ -31,10 +31,10 @@ excludes the point itself and breaks distance ties by the smaller index.
 
 Parity pins: see tests/test_oracle_pins.py (closed forms, invariants, brute
 force against a second, sort-based route, hand-derived golden values).
-The MBE pipeline end to end is pinned only by invariants (exact power-of-two
-scale invariance, permutation invariance, the uniform-lattice interior, the
-zero-pilot cap): for its absolute values it is "parity unpinned", since the
-paper prints no density values for any input.
+The MBE pipeline end to end is pinned by absolute values on a hand-derived
+case whose every stage is a closed form (tests/golden/mbe_chain.json), and by
+invariants on clouds too large for that (exact power-of-two scale invariance,
+permutation invariance, the uniform-lattice interior, the zero-pilot cap).
 """
 from __future__ import annotations
 

@@ -281,6 +281,54 @@ def test_mbe_zero_pilot_gives_cap():
     assert np.all(ell_in[~zero] < 5 * out["s"])
 
 
+def test_mbe_chain_golden(golden_dir):
+    """The whole estimator on a hand-derived case (every stage a closed form): Eq. 1 from
+    the coordinate percentiles, pilot values on nodes, trilinear pDen at particles sitting
+    on nodes, aveDen, l^(j) and the final node values with their per-axis fall-off.
+    Catches: a sum reading of Eq. 5 (aveDen x 10), a missing cube root or an inverted ratio
+    in Eq. 6, N instead of N_B (an eleventh particle lies outside B), log10 or a dropped
+    factor 2 in Eq. 1, another percentile rule (nearest rank makes P80 = P20), swapped
+    trilinear weights (they would read the neighbour node), transposed axes (the box is
+    anisotropic) and a node-wise instead of particle-wise l^(j) (the A and permutation
+    sites reach their diagonal neighbours differently)."""
+    g = _load(golden_dir, "mbe_chain.json")
+    edge = np.array(g["box"][1], dtype=np.float64)
+    xyz = (np.array(g["points_edge_units"]) * edge).astype(np.float32)
+    dims = tuple(g["dims"])
+    out = oracle.mbe(xyz, g["box"], dims, kernel=oracle.EPAN)
+
+    l = 0.4 / math.log(10.0)
+    U = 15.0 / (8.0 * math.pi * 10 * (l * edge[0]) * (l * edge[1]) * (l * edge[2]))
+    lA, lP = l * 0.55 ** (1.0 / 3.0), l * 2.2 ** (1.0 / 3.0)
+    at = lambda f, i, j, k: f[i + dims[0] * (j + dims[1] * k)] / U
+
+    assert out["nb"] == 10
+    np.testing.assert_allclose(out["ell0"], l * edge, rtol=1e-14)
+    assert at(out["pilot"], 4, 4, 4) == pytest.approx(4.0, rel=1e-13)
+    assert at(out["pilot"], 5, 4, 4) == pytest.approx(4.0 * (1 - (0.125 / l) ** 2), rel=1e-13)
+    np.testing.assert_allclose(out["pden"] / U, [4, 4, 4, 4, 1, 1, 1, 1, 1, 1], rtol=1e-13)
+    assert out["aveden"] / U == pytest.approx(2.2, rel=1e-13)
+    mem = out["member"]
+    assert mem.sum() == 10 and not mem[10]
+    ratio = np.array([0.55] * 4 + [2.2] * 6) ** (1.0 / 3.0)
+    np.testing.assert_allclose(out["ell_j"][mem], ratio[:, None] * (l * edge)[None, :], rtol=1e-13)
+
+    rho = out["final"]["rho"]
+    expect = {
+        (4, 4, 4): 80.0 / 11.0,
+        (5, 4, 4): 80.0 / 11.0 * (1 - (0.125 / lA) ** 2),
+        (5, 5, 4): 0.0,
+        (0, 4, 8): 5.0 / 11.0,
+        (1, 5, 8): 5.0 / 11.0 * (1 - 2 * (0.125 / lP) ** 2),
+        (1, 5, 7): 5.0 / 11.0 * (1 - 3 * (0.125 / lP) ** 2),
+        (2, 4, 8): 0.0,
+        (2, 2, 2): 0.0,
+    }
+    for node in g["final"]:
+        ijk = tuple(node["ijk"])
+        assert at(rho, *ijk) == pytest.approx(expect[ijk], rel=1e-12, abs=1e-300), ijk
+
+
 def test_mbe_scale_and_permutation_invariance():
     """The whole estimator (Eqs. 1, 2, 5, 6, 7) under coordinates and box times 2^3: the
     percentiles, l_k, s_k and l^(j) scale by 8 and every density by 2^-9, bit for bit
