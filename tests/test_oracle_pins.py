@@ -65,6 +65,40 @@ def test_epan_nodes_golden(golden_dir):
         assert v == pytest.approx(expect[(i, j, k)], rel=1e-13, abs=1e-300)
 
 
+def test_gauss_nodes_golden(golden_dir):
+    """Hand-derived truncated-Gaussian node values: peak 1/(N (2 pi)^1.5 l_x l_y l_z P3),
+    fall-off exp(-q/2) per axis and on diagonals, zero beyond q = 9 and non-zero up to it.
+    P3 comes from scipy's chi^2 CDF, not from the oracle. Catches exp(-q) for exp(-q/2),
+    a cutoff at q = 1 or 4 (Epanechnikov-like support), a missing P3 or (2 pi)^1.5, and
+    transposed bandwidth axes."""
+    stats = pytest.importorskip("scipy.stats")
+    g = _load(golden_dir, "gauss_nodes.json")
+    xyz = np.array(g["points"], dtype=np.float32)
+    l = np.array(g["ell"], dtype=np.float64)
+    dims = g["dims"]
+    out = oracle.kde_grid(xyz, np.tile(l, (xyz.shape[0], 1)), g["box"], dims, oracle.GAUSS3,
+                          oracle.SCOPE_GLOBAL)
+    peak = 0.25 / ((2.0 * math.pi) ** 1.5 * 0.1 * 0.2 * 0.15 * stats.chi2.cdf(9.0, 3))
+    q = {
+        (4, 4, 4): 0.0,
+        (5, 4, 4): 1.5625,
+        (3, 4, 4): 1.5625,
+        (4, 6, 4): 1.5625,
+        (4, 4, 6): 25.0 / 9.0,
+        (6, 4, 4): 6.25,
+        (6, 5, 5): 6.25 + 0.390625 + 25.0 / 36.0,
+        (6, 6, 5): 6.25 + 1.5625 + 25.0 / 36.0,
+    }
+    zero = {(6, 6, 6), (7, 4, 4)}
+    for node in g["nodes"]:
+        ijk = tuple(node["ijk"])
+        v = out["rho"][ijk[0] + dims[0] * (ijk[1] + dims[1] * ijk[2])]
+        if ijk in zero:
+            assert v == 0.0, ijk
+        else:
+            assert v == pytest.approx(peak * math.exp(-q[ijk] / 2.0), rel=1e-13), ijk
+
+
 def test_index_layout_argmax():
     """One off-centre particle: the maximum sits at flat index i_x + i_y*nx + i_z*nx*ny."""
     dims = (9, 7, 5)
