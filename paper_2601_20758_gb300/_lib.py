@@ -3,6 +3,9 @@
 Argument marshalling only: every step of the computation runs in the CUDA
 library. Functions keep the C names; tensors are passed as device pointers
 (``tensor.data_ptr()``), streams as ``torch.cuda.Stream.cuda_stream`` (or 0).
+The ABI's bare pointers carry no sizes, so before a pointer crosses it the
+binding checks that the tensor is a contiguous CUDA buffer of the element type
+and at least the length the header states, and raises ValueError otherwise.
 There is no CPU fallback: importing this module on a machine without the built
 library raises.
 """
@@ -132,6 +135,38 @@ def _check(fn, st):
     return st
 
 
+def _dev_buf(t, name, kind, min_numel):
+    """Check a device buffer before its pointer crosses the C ABI, which cannot see
+    sizes: a contiguous CUDA tensor of the element kind the header states ('f32'
+    float32, 'u32' 32-bit integer ids, 'u8' byte mask) holding at least min_numel
+    elements. Raises ValueError otherwise, so a short buffer never reaches a kernel."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    dt = t.dtype
+    ok = {"f32": dt.is_floating_point and dt.itemsize == 4,
+          "u32": not dt.is_floating_point and not dt.is_complex and dt.itemsize == 4,
+          "u8": not dt.is_floating_point and not dt.is_complex and dt.itemsize == 1}[kind]
+    if not ok:
+        raise ValueError(f"{name}: element type {dt} does not match {kind}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name}: {t.numel()} elements, {min_numel} needed")
+    return t.data_ptr()
+
+
+def _dims3(dims):
+    d = [int(v) for v in dims]
+    if len(d) != 3:
+        raise ValueError(f"dims: expected 3 values, got {len(d)}")
+    return d
+
+
+class sf_batch_handle(ctypes.c_void_p):
+    """Batch plan handle; remembers each ROI's node count so that sf_batch_run can
+    check the output buffers it is given."""
+
+
 def _stream(stream):
     if stream is None:
         return None
@@ -165,9 +200,11 @@ def make_params(rule=SF_BW_KNN, k=32, fixed_h=(0.0, 0.0, 0.0), cap_factor=5.0, p
 # ---------------------------------------------------------------------------
 def sf_build_index(d_xyz, stream=None):
     """d_xyz: CUDA float32 tensor [N, 3], contiguous. Returns the index handle."""
-    assert d_xyz.is_cuda and d_xyz.dtype.itemsize == 4 and d_xyz.is_contiguous()
+    if d_xyz.dim() != 2 or d_xyz.shape[1] != 3:
+        raise ValueError(f"d_xyz: expected shape [N, 3], got {tuple(d_xyz.shape)}")
+    ptr = _dev_buf(d_xyz, "d_xyz", "f32", 3 * d_xyz.shape[0])
     h = _vp()
-    _check("sf_build_index", load().sf_build_index(d_xyz.data_ptr(), d_xyz.shape[0],
+    _check("sf_build_index", load().sf_build_index(ptr, d_xyz.shape[0],
                                                    _stream(stream), ctypes.byref(h)))
     return h
 
@@ -181,62 +218,87 @@ def sf_bandwidths(idx, params, stream=None):
 
 
 def sf_get_bandwidths(idx, d_h, stream=None):
-    _check("sf_get_bandwidths", load().sf_get_bandwidths(idx, d_h.data_ptr(), _stream(stream)))
+    ptr = _dev_buf(d_h, "d_h", "f32", sf_index_size(idx))
+    _check("sf_get_bandwidths", load().sf_get_bandwidths(idx, ptr, _stream(stream)))
 
 
 def sf_knn_neighbours(idx, k, d_nbr, d_h=None, stream=None):
-    _check("sf_knn_neighbours", load().sf_knn_neighbours(
-        idx, int(k), d_nbr.data_ptr(), None if d_h is None else d_h.data_ptr(), _stream(stream)))
+    n = sf_index_size(idx)
+    pn = _dev_buf(d_nbr, "d_nbr", "u32", n * max(int(k), 0))
+    ph = None if d_h is None else _dev_buf(d_h, "d_h", "f32", n)
+    _check("sf_knn_neighbours", load().sf_knn_neighbours(idx, int(k), pn, ph, _stream(stream)))
 
 
 def sf_kde_grid(idx, roi: sf_box, dims, kernel, params, d_out, want_mass=False, stream=None):
     """Density on the ROI grid into d_out (float32, dims[2]*dims[1]*dims[0]); returns the
     FP64 mass when want_mass."""
-    d = (_i32 * 3)(*[int(v) for v in dims])
+    dd = _dims3(dims)
+    ptr = _dev_buf(d_out, "d_out", "f32", max(dd[0], 0) * max(dd[1], 0) * max(dd[2], 0))
+    d = (_i32 * 3)(*dd)
     m = _dbl(0.0)
     _check("sf_kde_grid", load().sf_kde_grid(idx, ctypes.byref(roi), d, int(kernel),
-                                             ctypes.byref(params), d_out.data_ptr(),
+                                             ctypes.byref(params), ptr,
                                              ctypes.byref(m) if want_mass else None,
                                              _stream(stream)))
     return m.value if want_mass else None
 
 
 def sf_kde_points(idx, roi: sf_box, dims, kernel, params, d_density, d_ids, stream=None) -> int:
-    """Densities of the ROI points (ascending original index); returns the count."""
-    d = None if dims is None else (_i32 * 3)(*[int(v) for v in dims])
+    """Densities of the ROI points (ascending original index); returns the count.
+    The capacity passed down is the shorter of the two buffers."""
+    d = None if dims is None else (_i32 * 3)(*_dims3(dims))
+    cap = min(d_density.numel(), d_ids.numel())
+    pd = _dev_buf(d_density, "d_density", "f32", cap)
+    pi = _dev_buf(d_ids, "d_ids", "u32", cap)
     cnt = _i64(0)
     _check("sf_kde_points", load().sf_kde_points(idx, ctypes.byref(roi), d, int(kernel),
-                                                 ctypes.byref(params), d_density.data_ptr(),
-                                                 d_ids.data_ptr(), d_density.numel(),
+                                                 ctypes.byref(params), pd, pi, cap,
                                                  ctypes.byref(cnt), _stream(stream)))
     return int(cnt.value)
 
 
 def sf_select(idx, d_density, d_ids, n, n_total, threshold=math.nan, percentile=90.0,
               d_mask=None, d_sel_ids=None, stream=None):
-    """Returns (count, threshold used)."""
+    """Returns (count, threshold used). d_density and d_ids may be None when n = 0."""
+    n, n_total = int(n), int(n_total)
+    pd = None if d_density is None else _dev_buf(d_density, "d_density", "f32", n)
+    pi = None if d_ids is None else _dev_buf(d_ids, "d_ids", "u32", n)
+    pm = None if d_mask is None else _dev_buf(d_mask, "d_mask", "u8", n_total)
+    ps = None if d_sel_ids is None else _dev_buf(d_sel_ids, "d_sel_ids", "u32", n)
     ns = _i64(0)
     t = _dbl(0.0)
-    _check("sf_select", load().sf_select(
-        idx, None if d_density is None else d_density.data_ptr(),
-        None if d_ids is None else d_ids.data_ptr(), int(n), int(n_total), float(threshold),
-        float(percentile), None if d_mask is None else d_mask.data_ptr(),
-        None if d_sel_ids is None else d_sel_ids.data_ptr(), ctypes.byref(ns), ctypes.byref(t),
-        _stream(stream)))
+    _check("sf_select", load().sf_select(idx, pd, pi, n, n_total, float(threshold),
+                                         float(percentile), pm, ps, ctypes.byref(ns),
+                                         ctypes.byref(t), _stream(stream)))
     return int(ns.value), float(t.value)
 
 
 def _boxes_dims(boxes, dims_list):
     n = len(boxes)
+    if len(dims_list) != n:
+        raise ValueError(f"{n} boxes but {len(dims_list)} dims")
+    flat = [_dims3(dd) for dd in dims_list]
     arr = (sf_box * n)(*boxes)
-    d = (_i32 * (3 * n))(*[int(v) for dd in dims_list for v in dd])
+    d = (_i32 * (3 * n))(*[v for dd in flat for v in dd])
     return n, arr, d
+
+
+def _node_counts(dims_list):
+    return [max(a, 0) * max(b, 0) * max(c, 0) for a, b, c in (_dims3(dd) for dd in dims_list)]
+
+
+def _out_ptrs(outs, nodes):
+    if len(outs) != len(nodes):
+        raise ValueError(f"{len(nodes)} ROIs but {len(outs)} output buffers")
+    return (_vp * len(outs))(*[_dev_buf(o, f"outs[{r}]", "f32", g)
+                               for r, (o, g) in enumerate(zip(outs, nodes))])
 
 
 def sf_batch_create(idx, boxes, dims_list, kernel, params, tune=None, stream=None):
     """Plan a batch of ROI grids (boxes: list of sf_box, dims_list: list of (nx, ny, nz))."""
     n, arr, d = _boxes_dims(boxes, dims_list)
-    h = _vp()
+    h = sf_batch_handle()
+    h.nodes = _node_counts(dims_list)
     _check("sf_batch_create", load().sf_batch_create(idx, n, arr, d, int(kernel), ctypes.byref(params),
                                                      None if tune is None else ctypes.byref(tune),
                                                      _stream(stream), ctypes.byref(h)))
@@ -245,7 +307,10 @@ def sf_batch_create(idx, boxes, dims_list, kernel, params, tune=None, stream=Non
 
 def sf_batch_run(batch, outs, want_mass=False, stream=None):
     n = len(outs)
-    ptrs = (_vp * n)(*[o.data_ptr() for o in outs])
+    nodes = getattr(batch, "nodes", None)
+    if nodes is None:      # a handle made elsewhere: element type and layout only
+        nodes = [0] * n
+    ptrs = _out_ptrs(outs, nodes)
     m = (_dbl * n)()
     _check("sf_batch_run", load().sf_batch_run(batch, ptrs, m if want_mass else None, _stream(stream)))
     return list(m) if want_mass else None
@@ -257,7 +322,7 @@ def sf_batch_free(batch):
 
 def sf_batch_kde_grid(idx, boxes, dims_list, kernel, params, outs, want_mass=False, stream=None):
     n, arr, d = _boxes_dims(boxes, dims_list)
-    ptrs = (_vp * n)(*[o.data_ptr() for o in outs])
+    ptrs = _out_ptrs(outs, _node_counts(dims_list))
     m = (_dbl * n)()
     _check("sf_batch_kde_grid", load().sf_batch_kde_grid(idx, n, arr, d, int(kernel), ctypes.byref(params),
                                                          ptrs, m if want_mass else None,

@@ -57,3 +57,73 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert lib.sf_select(None, None, None, -1, 0, 0.0, 0.0, None, None, None, None, None) == \
         _lib.SF_ERR_INVALID_ARG
     assert lib.sf_launch_count() == n0
+
+
+class _FakeDev:
+    """Stands in for a CUDA tensor in the binding's buffer checks (no GPU here); its
+    pointer is never dereferenced because every case below is rejected first."""
+
+    def __init__(self, n, dtype, contiguous=True, shape=None):
+        self.n, self.dtype, self.is_cuda, self._c = n, dtype, True, contiguous
+        self.shape = shape if shape is not None else (n,)
+
+    def numel(self):
+        return self.n
+
+    def is_contiguous(self):
+        return self._c
+
+    def dim(self):
+        return len(self.shape)
+
+    def data_ptr(self):
+        return 0
+
+
+def test_binding_rejects_unfit_buffers(lib):
+    """The C ABI takes bare pointers and cannot see a buffer's size, so the binding
+    refuses short, mistyped, strided or host buffers before any pointer crosses it."""
+    torch = pytest.importorskip("torch")
+    from paper_2601_20758_gb300 import _lib as L
+    p = L.make_params()
+    box = L.make_box((0, 0, 0), (1, 1, 1))
+    f32, i32, u8, f16 = torch.float32, torch.int32, torch.uint8, torch.float16
+    cases = [
+        (lambda: L.sf_build_index(torch.zeros(10, 3)), "CUDA"),
+        (lambda: L.sf_build_index(_FakeDev(30, i32, shape=(10, 3))), "element type"),
+        (lambda: L.sf_build_index(_FakeDev(40, f32, shape=(10, 4))), "shape"),
+        (lambda: L.sf_build_index(_FakeDev(30, f32, contiguous=False, shape=(10, 3))), "contiguous"),
+        (lambda: L.sf_kde_grid(None, box, (4, 4, 4), 0, p, _FakeDev(63, f32)), "64 needed"),
+        (lambda: L.sf_kde_grid(None, box, (4, 4, 4), 0, p, _FakeDev(64, f16)), "element type"),
+        (lambda: L.sf_kde_grid(None, box, (4, 4), 0, p, _FakeDev(64, f32)), "3 values"),
+        (lambda: L.sf_kde_points(None, box, None, 0, p, _FakeDev(8, f32), _FakeDev(8, f32)), "element type"),
+        (lambda: L.sf_select(None, _FakeDev(9, f32), _FakeDev(10, i32), 10, 20), "10 needed"),
+        (lambda: L.sf_select(None, _FakeDev(10, f32), _FakeDev(10, i32), 10, 20,
+                             d_mask=_FakeDev(19, u8)), "20 needed"),
+        (lambda: L.sf_select(None, _FakeDev(10, f32), _FakeDev(10, i32), 10, 20,
+                             d_sel_ids=_FakeDev(10, f32)), "element type"),
+        (lambda: L.sf_batch_kde_grid(None, [box, box], [(4, 4, 4), (8, 8, 8)], 0, p,
+                                     [_FakeDev(64, f32), _FakeDev(511, f32)]), "512 needed"),
+        (lambda: L.sf_batch_kde_grid(None, [box], [(4, 4, 4)], 0, p, []), "output buffers"),
+        (lambda: L.sf_batch_kde_grid(None, [box, box], [(4, 4, 4)], 0, p, []), "dims"),
+    ]
+    for call, words in cases:
+        with pytest.raises(ValueError, match=words):
+            call()
+
+
+def test_binding_passes_the_shorter_capacity(lib, monkeypatch):
+    """sf_kde_points hands the library the length of the shorter of its two buffers."""
+    torch = pytest.importorskip("torch")
+    from paper_2601_20758_gb300 import _lib as L
+    seen = {}
+
+    class _Lib:
+        def sf_kde_points(self, idx, roi, dims, kernel, params, pd, pi, cap, h_count, stream):
+            seen["cap"] = cap
+            return L.SF_OK
+
+    monkeypatch.setattr(L, "load", lambda: _Lib())
+    L.sf_kde_points(None, L.make_box((0, 0, 0), (1, 1, 1)), None, 0, L.sf_params(),
+                    _FakeDev(100, torch.float32), _FakeDev(60, torch.int32))
+    assert seen["cap"] == 60
