@@ -438,3 +438,43 @@ def test_ambiguous_mass_is_two_sided():
         val = np.exp(-0.5 * q) / ((2 * np.pi) ** 1.5 * h ** 3 * oracle.P3)
         assert out["amb"][0] == pytest.approx(val, rel=1e-12)
         assert out["rho"][0] == (pytest.approx(val, rel=1e-12) if inside else 0.0)
+
+
+# --------------------------------------------------------------------------
+# The per-node side outputs of the density sum: wpeak and pairs
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("scope", [oracle.SCOPE_GLOBAL, oracle.SCOPE_CLIP])
+@pytest.mark.parametrize("kernel", [oracle.EPAN, oracle.GAUSS3])
+def test_wpeak_and_pairs_golden(golden_dir, kernel, scope):
+    """wpeak = (1/N_eff) x the sum of the peaks C/(l_x l_y l_z) of the in-support particles,
+    pairs = their count, on hand-derived cases with particles exactly on the cutoff
+    (q = 1 for Epanechnikov, q = 9 for the Gaussian). wpeak scales every density tolerance
+    and pairs is the benchmark's work unit. Catches a dropped 1/N_eff (a factor 5 or 4),
+    N for N_B in the clip scope, q <= qmax for q < qmax (one more pair and peak on the
+    boundary), peaks summed outside the support, and a peak without the 1/(l_x l_y l_z)."""
+    stats = pytest.importorskip("scipy.stats")
+    g = _load(golden_dir, "support_counts.json")
+    xyz = np.array(g["points"], dtype=np.float32)
+    ell = np.array(g["ell"], dtype=np.float64)
+    names = g["names"]
+    dims = g["dims"]
+    out = oracle.kde_grid(xyz, ell, g["box"], dims, kernel, scope)
+    neff = 5 if scope == oracle.SCOPE_GLOBAL else 4
+    assert out["neff"] == neff
+    if kernel == oracle.EPAN:
+        cnorm = 15.0 / (8.0 * math.pi)
+    else:
+        cnorm = 1.0 / ((2.0 * math.pi) ** 1.5 * stats.chi2.cdf(9.0, 3))
+    peak = {nm: cnorm / float(np.prod(ell[i])) for i, nm in enumerate(names)}
+    for node in g["nodes"]:
+        i, j, k = node["ijk"]
+        flat = i + j * dims[0] + k * dims[0] * dims[1]
+        inside = node["epan_in"] if kernel == oracle.EPAN else node["gauss_in"]
+        assert int(out["pairs"][flat]) == len(inside), (node["ijk"], out["pairs"][flat])
+        expect = sum(peak[nm] for nm in inside) / neff
+        assert out["wpeak"][flat] == pytest.approx(expect, rel=1e-13), node["ijk"]
+        if kernel == oracle.GAUSS3:
+            # the particle on the cutoff adds nothing to rho, and its untruncated
+            # kernel value exp(-9/2) * peak to the ambiguous mass
+            amb = sum(peak[nm] * math.exp(-4.5) for nm in node["gauss_boundary"]) / neff
+            assert out["amb"][flat] == pytest.approx(amb, rel=1e-13, abs=1e-300), node["ijk"]
