@@ -172,8 +172,8 @@ sf_status sf_knn_neighbours(sf_index *idx, int32_t k, uint32_t *d_nbr, float *d_
  * Errors: INVALID_ARG, OOM, CUDA, DEGENERATE (MBE with N_B < 2 or P80 == P20),
  * EMPTY_ROI (scope CLIP and no point in B; d_out is zero-filled), CAPACITY (the
  * per-tile candidate lists would exceed 2^31 entries: fewer nodes or a smaller ROI).
- * Device-side degenerate conditions are reported by the next call that
- * synchronises (h_mass given, or sf_sync_status).
+ * The call synchronises the stream once to size its work lists (before the
+ * density kernels run); EMPTY_ROI is returned by the call itself.
  */
 sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], int32_t kernel,
                       const sf_params *params, float *d_out, double *h_mass, void *stream);
@@ -186,6 +186,12 @@ sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], i
  * density. capacity = length of both buffers; *h_count (host, required)
  * receives the number of ROI points (the stream is synchronised). If the
  * count exceeds capacity, CAPACITY is returned and nothing is written.
+ * The ROI's points are found through the index (the leaves whose bounding box
+ * meets the box), so for the kNN and fixed rules the call's time and scratch
+ * grow with the ROI's points, not with the cloud: about 24 bytes per ROI point
+ * plus 9 bytes per point of the leaves that meet the box (sf_query_workspace
+ * gives the exact figure). Rule MBE also needs 16 bytes per cloud point.
+ * Scope CLIP with no point in B returns EMPTY_ROI with *h_count = 0.
  * DIRECT sums the kernels at each point (the point's own kernel included);
  * INTERP interpolates the grid of the same dims trilinearly.
  * params->prec TF32 / 3XTF32 / BF16 (DIRECT with kNN bandwidths only): the
@@ -201,6 +207,29 @@ sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], i
 sf_status sf_kde_points(sf_index *idx, const sf_box *roi, const int32_t *dims, int32_t kernel,
                         const sf_params *params, float *d_density, uint32_t *d_ids,
                         int64_t capacity, int64_t *h_count, void *stream);
+
+/*
+ * sf_query_workspace -- the device memory a call would allocate, before it is
+ * made (admission by memory in a serving loop).
+ *
+ * what = SF_WS_GRID: sf_kde_grid(idx, roi, dims, kernel, params, ..., h_mass)
+ * with h_mass given; SF_WS_POINTS: sf_kde_points(idx, roi, dims, kernel,
+ * params, ...). *h_bytes (host) receives the most stream-ordered scratch the
+ * call holds at once (each allocation rounded up to 256 bytes; the device's
+ * pool may round further). The grid figure is exact: it runs the call's
+ * candidate count for this ROI (an index walk per node tile). The points
+ * figure counts the ROI's leaves and bounds the ROI's points by 32 per leaf.
+ * Synchronises the stream. Rules SF_BW_KNN and SF_BW_FIXED (the MBE rule's
+ * workspace depends on its per-ROI lengths: INVALID_ARG). Errors: INVALID_ARG,
+ * OOM, CUDA.
+ */
+enum { SF_WS_GRID = 1, SF_WS_POINTS = 2 };
+sf_status sf_query_workspace(sf_index *idx, const sf_box *roi, const int32_t *dims, int32_t kernel,
+                             const sf_params *params, int32_t what, int64_t *h_bytes, void *stream);
+
+/* The most stream-ordered scratch (bytes, counted as sf_query_workspace counts
+ * it) that the calling thread's most recent library call held at once. */
+int64_t sf_last_call_workspace(void);
 
 /*
  * sf_select -- density-threshold selection of points (Sec. 4.1).
@@ -281,7 +310,9 @@ sf_status sf_batch_kde_grid(sf_index *idx, int32_t nroi, const sf_box *rois, con
  * before any stream capture. Every call shares the one array and leaves its
  * contents behind for the next: calls that overlap on the GPU (different
  * streams, or different host threads, at the same time) race on it and must
- * be serialised by the caller. h_mass as for sf_kde_grid.
+ * be serialised by the caller. h_mass as for sf_kde_grid; the call
+ * synchronises only when h_mass is given, and only then reports EMPTY_ROI
+ * (without h_mass an empty clip-scope ROI yields the zero grid and SF_OK).
  */
 sf_status sf_kde_grid_static(sf_index *idx, const sf_box *roi, const int32_t dims[3],
                              int32_t kernel, const sf_params *params, float *d_out,
@@ -314,7 +345,9 @@ sf_status sf_kernel_timing(const char *name, double *h_ms_total, int64_t *h_laun
 sf_status sf_kernel_timing_list(const char *name, double *h_ms, int64_t cap, int64_t *h_count);
 
 /* Synchronise `stream` and return (then clear) any status a kernel recorded
- * on the device for this index (TIMEOUT, DEGENERATE, EMPTY_ROI). */
+ * on the device for this index. Every call returns the statuses of its own
+ * kernels itself (each call has its own status word), so this reports only
+ * CUDA errors of work still queued on the stream. */
 sf_status sf_sync_status(sf_index *idx, void *stream);
 
 /* Release the index and all of its device memory. Safe on NULL. */

@@ -41,6 +41,8 @@ SF_PREC_3XTF32 = 2
 SF_PREC_BF16 = 3
 SF_POINTS_DIRECT = 0
 SF_POINTS_INTERP = 1
+SF_WS_GRID = 1
+SF_WS_POINTS = 2
 
 STATUS_NAMES = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_OOM", 3: "SF_ERR_CUDA",
                 4: "SF_ERR_TIMEOUT", 5: "SF_ERR_DEGENERATE", 6: "SF_ERR_EMPTY_ROI",
@@ -100,6 +102,9 @@ _PROTOS = {
                                               ctypes.POINTER(_i64), _vp]),
     "sf_kde_grid_static": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
                                           ctypes.POINTER(sf_params), _vp, ctypes.POINTER(_dbl), _vp]),
+    "sf_query_workspace": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
+                                          ctypes.POINTER(sf_params), _i32, ctypes.POINTER(_i64), _vp]),
+    "sf_last_call_workspace": (_i64, []),
     "sf_kernel_timing_enable": (None, [ctypes.c_int]),
     "sf_kernel_timing_reset": (None, []),
     "sf_kernel_timing": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
@@ -255,6 +260,22 @@ def sf_kde_points(idx, roi: sf_box, dims, kernel, params, d_density, d_ids, stre
                                                  ctypes.byref(params), pd, pi, cap,
                                                  ctypes.byref(cnt), _stream(stream)))
     return int(cnt.value)
+
+
+def sf_query_workspace(idx, roi: sf_box, dims, kernel, params, what=SF_WS_GRID, stream=None) -> int:
+    """Device bytes the grid (SF_WS_GRID, with the mass) or points (SF_WS_POINTS) call for
+    this ROI would allocate at most at once."""
+    d = None if dims is None else (_i32 * 3)(*_dims3(dims))
+    b = _i64(0)
+    _check("sf_query_workspace", load().sf_query_workspace(idx, ctypes.byref(roi), d, int(kernel),
+                                                           ctypes.byref(params), int(what),
+                                                           ctypes.byref(b), _stream(stream)))
+    return int(b.value)
+
+
+def sf_last_call_workspace() -> int:
+    """Peak scratch bytes of the calling thread's most recent library call."""
+    return int(load().sf_last_call_workspace())
 
 
 def sf_select(idx, d_density, d_ids, n, n_total, threshold=math.nan, percentile=90.0,

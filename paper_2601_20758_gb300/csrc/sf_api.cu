@@ -15,16 +15,23 @@ sf_status scatter_bandwidths(const sf_index *idx, float *d_h_orig, cudaStream_t 
 sf_status select_points(const float *d_density, const uint32_t *d_ids, int64_t n, int64_t n_total,
                         double threshold, double percentile, uint8_t *d_mask, uint32_t *d_sel_ids,
                         int64_t *h_nsel, double *h_threshold, cudaStream_t s);
-sf_status compact_roi_points(sf_index *idx, const uint8_t *d_inroi, const float *d_rho_sorted,
-                             float *d_density, uint32_t *d_ids, int64_t capacity,
-                             int64_t *h_count, cudaStream_t s);
+sf_status roi_leaf_list(sf_index *idx, const sf_box &roi, Scratch &sc, int **d_list,
+                        int64_t *h_nleaf, StatusPeek *peek, cudaStream_t s);
+sf_status roi_compact(sf_index *idx, const int *d_leaves, int64_t nslots, const uint8_t *d_inroi,
+                      const float *d_rho, float *d_density, uint32_t *d_ids, int64_t capacity,
+                      int64_t *h_count, cudaStream_t s);
+sf_status grid_workspace(sf_index *idx, const sf_box &roi, const GridSpec &g,
+                         const DensityCall &call, int64_t *bytes, cudaStream_t s);
+sf_status points_workspace(sf_index *idx, const sf_box &roi, const GridSpec *g,
+                           const DensityCall &call, int64_t base_bytes, int64_t *bytes,
+                           cudaStream_t s);
+int64_t last_call_scratch_peak();
 sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int kernel,
                       const sf_params &p, DensityParams *d_dp, float4 *d_ell, float4 *d_nell,
                       float *d_pilot, cudaStream_t s);
 sf_status interp_points(sf_index *idx, const sf_box &roi, const GridSpec &g, const float *d_grid,
-                        float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s);
-sf_status density_points_tc(sf_index *idx, const sf_box &roi, const DensityCall &call, int prec,
-                            float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s);
+                        const int *d_leaves, int64_t nslots, float *d_rho_sorted, uint8_t *d_inroi,
+                        cudaStream_t s);
 
 // Count the points of the scope and set N_eff (device); EMPTY_ROI is recorded
 // in the status word when the clip scope holds no point.
@@ -54,7 +61,7 @@ __global__ void k_set_params(DensityParams *dp, const unsigned long long *cnt, i
 }
 
 sf_status set_density_params(sf_index *idx, bool clip, const sf_box &roi, const float ell[3],
-                             DensityParams *d_dp, cudaStream_t s) {
+                             DensityParams *d_dp, int *d_status, cudaStream_t s) {
     unsigned long long *cnt = nullptr;
     Scratch sc(s);
     if (clip) {
@@ -78,8 +85,7 @@ sf_status set_density_params(sf_index *idx, bool clip, const sf_box &roi, const 
                            lo, hi, cnt));
     }
     SF_TRY_CUDA(launch(k_set_params, dim3(1), dim3(1), 0, s, d_dp,
-                       (const unsigned long long *)cnt, idx->n, ell[0], ell[1], ell[2],
-                       idx->d_status));
+                       (const unsigned long long *)cnt, idx->n, ell[0], ell[1], ell[2], d_status));
     return SF_OK;
 }
 
@@ -143,6 +149,7 @@ static sf_status make_grid(const sf_box &roi, const int32_t *dims, GridSpec &g, 
 struct Prepared {
     DensityCall call;
     DensityParams *dp = nullptr;
+    int *status = nullptr;  // this call's device status word (ST_EMPTY in clip scope)
     float4 *ell = nullptr;
     float4 *nell = nullptr;
 };
@@ -150,7 +157,9 @@ struct Prepared {
 static sf_status prepare(sf_index *idx, const sf_box &roi, const GridSpec *g, int kernel,
                          const sf_params &p, Scratch &sc, Prepared &out, cudaStream_t s) {
     out.dp = sc.get<DensityParams>(1);
+    out.status = sc.get<int>(1);
     SF_TRY_SCRATCH(sc);
+    SF_TRY_CUDA(cudaMemsetAsync(out.status, 0, sizeof(int), s));
     out.call.kernel = kernel;
     out.call.dp = out.dp;
     out.call.ell = nullptr;
@@ -176,7 +185,14 @@ static sf_status prepare(sf_index *idx, const sf_box &roi, const GridSpec *g, in
     } else {
         out.call.bw = BW_ISO;
     }
-    SF_TRY(set_density_params(idx, clip, roi, ell, out.dp, s));
+    SF_TRY(set_density_params(idx, clip, roi, ell, out.dp, out.status, s));
+    return SF_OK;
+}
+
+// The status a call's kernels recorded, as the call's return value.
+static sf_status call_status(int st) {
+    if (st == ST_EMPTY) return fail(SF_ERR_EMPTY_ROI, "no particle of the scope lies in the ROI");
+    if (st != ST_OK) return fail((sf_status)st, "device reported status %d", st);
     return SF_OK;
 }
 
@@ -263,12 +279,14 @@ sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], i
     SF_TRY_SCRATCH(sc);
     Prepared pr;
     SF_TRY(prepare(idx, *roi, &g, kernel, *params, sc, pr, s));
-    SF_TRY(density_grid(idx, *roi, g, pr.call, d_out, d_mass, s));
+    StatusPeek peek;
+    peek.d_src = pr.status;
+    SF_TRY(density_grid(idx, *roi, g, pr.call, d_out, d_mass, s, nullptr, &peek));
     if (h_mass) {
         SF_TRY_CUDA(cudaMemcpyAsync(h_mass, d_mass, sizeof(double), cudaMemcpyDeviceToHost, s));
-        return sf_sync_status(idx, stream);
+        SF_TRY_CUDA(cudaStreamSynchronize(s));
     }
-    return SF_OK;
+    return call_status(peek.value);
 }
 
 sf_status sf_kde_points(sf_index *idx, const sf_box *roi, const int32_t *dims, int32_t kernel,
@@ -280,32 +298,76 @@ sf_status sf_kde_points(sf_index *idx, const sf_box *roi, const int32_t *dims, i
     if (capacity < 0) return fail(SF_ERR_INVALID_ARG, "sf_kde_points: negative capacity");
     SF_TRY(check_roi(roi, "sf_kde_points"));
     SF_TRY(check_params(idx, params, kernel, "sf_kde_points"));
+    if (params->prec != SF_PREC_FP32 &&
+        (params->rule != SF_BW_KNN || params->points_mode != SF_POINTS_DIRECT))
+        return fail(SF_ERR_INVALID_ARG, "sf_kde_points: TF32 / 3xTF32 / BF16 need rule KNN and DIRECT");
     GridSpec g;
     const bool need_grid = params->rule == SF_BW_MBE || params->points_mode == SF_POINTS_INTERP;
     if (need_grid) SF_TRY(make_grid(*roi, dims, g, "sf_kde_points"));
     cudaStream_t s = (cudaStream_t)stream;
+    *h_count = 0;
     Scratch sc(s);
-    float *rho = sc.get<float>(idx->n);
-    uint8_t *inroi = sc.get<uint8_t>(idx->n);
-    SF_TRY_SCRATCH(sc);
     Prepared pr;
     SF_TRY(prepare(idx, *roi, need_grid ? &g : nullptr, kernel, *params, sc, pr, s));
-    if (params->prec != SF_PREC_FP32 &&
-        (params->rule != SF_BW_KNN || params->points_mode != SF_POINTS_DIRECT))
-        return fail(SF_ERR_INVALID_ARG, "sf_kde_points: TF32 / 3xTF32 / BF16 need rule KNN and DIRECT");
+    // the leaves that can hold an ROI point (one synchronisation)
+    StatusPeek peek;
+    peek.d_src = pr.status;
+    int *leaves = nullptr;
+    int64_t nleaf = 0;
+    SF_TRY(roi_leaf_list(idx, *roi, sc, &leaves, &nleaf, &peek, s));
+    if (peek.value != ST_OK || nleaf == 0) return call_status(peek.value);
+    float *rho = sc.get<float>(nleaf * kLeaf);
+    uint8_t *inroi = sc.get<uint8_t>(nleaf * kLeaf);
+    SF_TRY_SCRATCH(sc);
     if (params->prec != SF_PREC_FP32) {
-        SF_TRY(density_points_tc(idx, *roi, pr.call, params->prec, rho, inroi, s));
+        SF_TRY(density_points_tc(idx, *roi, pr.call, params->prec, leaves, nleaf, rho, inroi, s));
     } else if (params->points_mode == SF_POINTS_INTERP) {
-        float *grid = sc.get<float>((int64_t)g.nx * g.ny * g.nz);
-        SF_TRY_SCRATCH(sc);
+        Scratch gs(s);
+        float *grid = gs.get<float>((int64_t)g.nx * g.ny * g.nz);
+        SF_TRY_SCRATCH(gs);
         SF_TRY(density_grid(idx, *roi, g, pr.call, grid, nullptr, s));
-        SF_TRY(interp_points(idx, *roi, g, grid, rho, inroi, s));
+        SF_TRY(interp_points(idx, *roi, g, grid, leaves, nleaf, rho, inroi, s));
     } else {
-        SF_TRY(density_points(idx, *roi, pr.call, rho, inroi, s));
+        SF_TRY(density_points(idx, *roi, pr.call, leaves, nleaf, rho, inroi, s));
     }
-    SF_TRY(compact_roi_points(idx, inroi, rho, d_density, d_ids, capacity, h_count, s));
-    return sf_sync_status(idx, stream);
+    SF_TRY(roi_compact(idx, leaves, nleaf, inroi, rho, d_density, d_ids, capacity, h_count, s));
+    return SF_OK;
 }
+
+sf_status sf_query_workspace(sf_index *idx, const sf_box *roi, const int32_t *dims, int32_t kernel,
+                             const sf_params *params, int32_t what, int64_t *h_bytes, void *stream) {
+    clear_error();
+    if (!idx || !h_bytes) return fail(SF_ERR_INVALID_ARG, "sf_query_workspace: NULL argument");
+    *h_bytes = 0;
+    if (what != SF_WS_GRID && what != SF_WS_POINTS)
+        return fail(SF_ERR_INVALID_ARG, "sf_query_workspace: what=%d is not SF_WS_GRID or SF_WS_POINTS", what);
+    SF_TRY(check_roi(roi, "sf_query_workspace"));
+    SF_TRY(check_params(idx, params, kernel, "sf_query_workspace"));
+    if (params->rule == SF_BW_MBE)
+        return fail(SF_ERR_INVALID_ARG,
+                    "sf_query_workspace: rule MBE's workspace depends on its adaptive lengths (kNN and fixed rules only)");
+    GridSpec g;
+    const bool need_grid = what == SF_WS_GRID || params->points_mode == SF_POINTS_INTERP;
+    if (need_grid) SF_TRY(make_grid(*roi, dims, g, "sf_query_workspace"));
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Prepared pr;
+    SF_TRY(prepare(idx, *roi, need_grid ? &g : nullptr, kernel, *params, sc, pr, s));
+    // what the entry point itself holds: its parameters and status word
+    const int64_t base = scratch_round(sizeof(DensityParams)) + scratch_round(sizeof(int));
+    int64_t b = 0;
+    if (what == SF_WS_GRID) {
+        SF_TRY(grid_workspace(idx, *roi, g, pr.call, &b, s));
+        b += base + scratch_round(sizeof(double));  // the mass word (h_mass given)
+    } else {
+        const bool interp = params->points_mode == SF_POINTS_INTERP && params->prec == SF_PREC_FP32;
+        SF_TRY(points_workspace(idx, *roi, interp ? &g : nullptr, pr.call, base, &b, s));
+    }
+    *h_bytes = b;
+    return SF_OK;
+}
+
+int64_t sf_last_call_workspace(void) { return last_call_scratch_peak(); }
 
 sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids, int64_t n,
                     int64_t n_total, double threshold, double percentile, uint8_t *d_mask,
@@ -346,17 +408,23 @@ sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t
         SF_TRY(density_grid(idx, *roi, g, pr.call, grid, nullptr, s, cnt));
     }
     if (h_point_pairs) {
-        float *rho = sc.get<float>(idx->n);
-        uint8_t *inroi = sc.get<uint8_t>(idx->n);
+        int *leaves = nullptr;
+        int64_t nleaf = 0;
+        SF_TRY(roi_leaf_list(idx, *roi, sc, &leaves, &nleaf, nullptr, s));
+        float *rho = sc.get<float>(nleaf * kLeaf);
+        uint8_t *inroi = sc.get<uint8_t>(nleaf * kLeaf);
         SF_TRY_SCRATCH(sc);
-        SF_TRY(density_points(idx, *roi, pr.call, rho, inroi, s, cnt + 1));
+        if (nleaf > 0)
+            SF_TRY(density_points(idx, *roi, pr.call, leaves, nleaf, rho, inroi, s, cnt + 1));
     }
     unsigned long long h[2] = {0, 0};
+    int h_st = 0;
     SF_TRY_CUDA(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, s));
+    SF_TRY_CUDA(cudaMemcpyAsync(&h_st, pr.status, sizeof h_st, cudaMemcpyDeviceToHost, s));
     SF_TRY_CUDA(cudaStreamSynchronize(s));
     if (h_grid_pairs) *h_grid_pairs = (int64_t)h[0];
     if (h_point_pairs) *h_point_pairs = (int64_t)h[1];
-    return sf_sync_status(idx, stream);
+    return call_status(h_st);
 }
 
 struct sf_batch {
@@ -394,6 +462,10 @@ sf_status sf_batch_create(sf_index *idx, int32_t nroi, const sf_box *rois, const
         SF_TRY(make_grid(rois[r], dims + 3 * r, grids[r], "sf_batch_create"));
     }
     cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    int *d_st = sc.get<int>(1);
+    SF_TRY_SCRATCH(sc);
+    SF_TRY_CUDA(cudaMemsetAsync(d_st, 0, sizeof(int), s));
     DensityParams *dps = nullptr;
     SF_TRY_CUDA(cudaMalloc(&dps, sizeof(DensityParams) * nroi));
     const bool clip = params->scope == SF_SCOPE_CLIP;
@@ -402,7 +474,7 @@ sf_status sf_batch_create(sf_index *idx, int32_t nroi, const sf_box *rois, const
     if (bw == BW_UNIFORM)
         for (int k = 0; k < 3; ++k) ell[k] = (float)params->fixed_h[k];
     for (int r = 0; r < nroi; ++r) {
-        sf_status st = set_density_params(idx, clip, rois[r], ell, dps + r, s);
+        sf_status st = set_density_params(idx, clip, rois[r], ell, dps + r, d_st, s);
         if (st != SF_OK) {
             cudaFree(dps);
             return st;
@@ -414,7 +486,10 @@ sf_status sf_batch_create(sf_index *idx, int32_t nroi, const sf_box *rois, const
     b->plan = plan;
     b->nroi = nroi;
     *out = b;
-    return sf_sync_status(idx, stream);
+    int h_st = 0;
+    SF_TRY_CUDA(cudaMemcpyAsync(&h_st, d_st, sizeof h_st, cudaMemcpyDeviceToHost, s));
+    SF_TRY_CUDA(cudaStreamSynchronize(s));
+    return call_status(h_st);  // EMPTY_ROI: some clip-scope ROI holds no particle (the plan is kept)
 }
 
 sf_status sf_batch_run(sf_batch *b, float *const *d_outs, double *h_masses, void *stream) {
@@ -438,11 +513,13 @@ sf_status sf_batch_kde_grid(sf_index *idx, int32_t nroi, const sf_box *rois, con
     memset(&t, 0, sizeof t);
     t.no_graph = 1;  // a one-shot batch gains nothing from a graph
     sf_batch *b = nullptr;
-    SF_TRY(sf_batch_create(idx, nroi, rois, dims, kernel, params, &t, stream, &b));
+    const sf_status cs = sf_batch_create(idx, nroi, rois, dims, kernel, params, &t, stream, &b);
+    if (cs != SF_OK && cs != SF_ERR_EMPTY_ROI) return cs;
+    // an empty clip-scope ROI still gets its (zero) grid
     sf_status st = sf_batch_run(b, d_outs, h_masses, stream);
-    if (st == SF_OK) st = sf_sync_status(idx, stream);
     sf_batch_free(b);
-    return st;
+    if (st != SF_OK) return st;
+    return cs == SF_OK ? SF_OK : fail(cs, "sf_batch_kde_grid: a clip-scope ROI holds no particle");
 }
 
 sf_status sf_sync_status(sf_index *idx, void *stream) {

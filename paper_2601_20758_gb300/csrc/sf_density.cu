@@ -1018,13 +1018,9 @@ __global__ void k_mr_mass(const RoiDesc *__restrict__ rois, const double *__rest
 template <int KER, int BW, bool CLIP, bool CNT>
 static cudaError_t launch_grid_t(const GridArgs &a, unsigned tiles, cudaStream_t s) {
     const size_t smem = sizeof(GridSmemT<kTileZ>);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_grid<KER, BW, CLIP, CNT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    cudaError_t e = smem_attr_once(k_grid<KER, BW, CLIP, CNT>, smem, attr);
+    if (e != cudaSuccess) return e;
     KTimer t(CNT ? "k_grid_count" : "k_grid", s);
     return launch(k_grid<KER, BW, CLIP, CNT>, dim3(tiles), dim3(kGridThreads), smem, s, a);
 }
@@ -1054,7 +1050,7 @@ template <int KER, int BW, bool CLIP, int TZ>
 // tot: 16 bytes -- [0] the 32-bit scan total, [1] the item count of mr_exec,
 // bytes 8..15 the same total summed in 64 bits (guards the 32-bit offsets).
 static sf_status mr_count(const MrArgs &a, uint32_t *cnt, uint32_t *off, uint32_t *tot,
-                          uint32_t *h_total, cudaStream_t s) {
+                          uint32_t *h_total, StatusPeek *peek, cudaStream_t s) {
     const unsigned wb = blocks_for(a.ntiles, kWalkWarps);
     SF_TRY_CUDA(launch(k_mr_walk<KER, BW, CLIP, false, TZ>, dim3(wb), dim3(kWalkWarps * 32), 0, s, a,
                        cnt, (const uint32_t *)nullptr, (int *)nullptr));
@@ -1065,6 +1061,8 @@ static sf_status mr_count(const MrArgs &a, uint32_t *cnt, uint32_t *off, uint32_
                        (const uint32_t *)cnt, a.ntiles, tot64));
     unsigned long long h64 = 0;
     SF_TRY_CUDA(cudaMemcpyAsync(&h64, tot64, sizeof h64, cudaMemcpyDeviceToHost, s));
+    if (peek && peek->d_src)
+        SF_TRY_CUDA(cudaMemcpyAsync(&peek->value, peek->d_src, sizeof(int), cudaMemcpyDeviceToHost, s));
     SF_TRY_CUDA(cudaStreamSynchronize(s));
     if (h64 > 0x7fffffffull)
         return fail(SF_ERR_CAPACITY, "grid candidate lists of %llu entries exceed 2^31; use fewer nodes or a smaller ROI",
@@ -1081,12 +1079,8 @@ static size_t mr_work_smem() {
 template <int KER, int BW, bool CLIP, bool CNT, int TZ>
 static sf_status mr_work_attr(int *per_sm) {
     const size_t smem = mr_work_smem<TZ>();
-    static bool attr = false;
-    if (!attr) {
-        SF_TRY_CUDA(cudaFuncSetAttribute(k_mr_work<KER, BW, CLIP, CNT, TZ>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    SF_TRY_CUDA(smem_attr_once(k_mr_work<KER, BW, CLIP, CNT, TZ>, smem, attr));
     SF_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_mr_work<KER, BW, CLIP, CNT, TZ>,
                                                               kGridThreads, smem));
     if (*per_sm < 1) *per_sm = 1;
@@ -1128,20 +1122,38 @@ static sf_status mr_exec(const MrArgs &a, const MrBuffers &b, cudaStream_t s) {
     return SF_OK;
 }
 
-// Plan the buffers of an execution from the candidate total.
+// Sizes of an execution from the candidate total: resident blocks, leaves per
+// work item, the item bound.
 template <int KER, int BW, bool CLIP, bool CNT, int TZ>
-static sf_status mr_plan(const MrArgs &a, uint32_t total, int items_per_slot, MrBuffers &b,
-                         Scratch *sc, std::vector<void *> *owned, cudaStream_t s) {
+static sf_status mr_sizes(const MrArgs &a, uint32_t total, int items_per_slot, int64_t *slots,
+                          uint32_t *lpw, int64_t *max_items) {
     int dev = 0, sms = 0, per_sm = 0;
     SF_TRY_CUDA(cudaGetDevice(&dev));
     SF_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SF_TRY((mr_work_attr<KER, BW, CLIP, CNT, TZ>(&per_sm)));
-    b.slots = (int64_t)sms * per_sm;  // resident blocks of 8 persistent warps
-    const int64_t warps = b.slots * (kGridThreads / 32);
+    *slots = (int64_t)sms * per_sm;  // resident blocks of 8 persistent warps
+    const int64_t warps = *slots * (kGridThreads / 32);
     const int64_t ips = std::max(1, items_per_slot);
-    uint32_t lpw = (uint32_t)std::max<int64_t>(8, (total + ips * warps - 1) / (ips * warps));
-    b.lpw = lpw;
-    const int64_t max_items = a.ntiles + total / b.lpw + 1;
+    *lpw = (uint32_t)std::max<int64_t>(8, (total + ips * warps - 1) / (ips * warps));
+    *max_items = a.ntiles + total / *lpw + 1;
+    return SF_OK;
+}
+
+// Bytes of the execution buffers mr_plan allocates (each rounded as Scratch counts it).
+template <int TZ>
+static int64_t mr_plan_bytes(int64_t ntiles, uint32_t total, int64_t max_items) {
+    return scratch_round(4 * std::max<int64_t>(1, total)) + 2 * scratch_round(4 * ntiles) +
+           scratch_round(16 * max_items) + scratch_round(8 * max_items * 32 * TZ) + scratch_round(4);
+}
+
+static int64_t scan_parts_bytes_(int64_t n) { return n > 0 ? scratch_round(4 * ((n + 2047) / 2048)) : 0; }
+
+// Plan the buffers of an execution from the candidate total.
+template <int KER, int BW, bool CLIP, bool CNT, int TZ>
+static sf_status mr_plan(const MrArgs &a, uint32_t total, int items_per_slot, MrBuffers &b,
+                         Scratch *sc, std::vector<void *> *owned, cudaStream_t s) {
+    int64_t max_items = 0;
+    SF_TRY((mr_sizes<KER, BW, CLIP, CNT, TZ>(a, total, items_per_slot, &b.slots, &b.lpw, &max_items)));
     auto get = [&](size_t bytes) -> void * {
         void *p = nullptr;
         if (sc) {
@@ -1164,8 +1176,10 @@ static sf_status mr_plan(const MrArgs &a, uint32_t total, int items_per_slot, Mr
     return SF_OK;
 }
 
+// ws_bytes (nullable): size the execution and return its bytes instead of running it.
 template <int KER, int BW, bool CLIP, int TZ>
-static sf_status mr_once(const MrArgs &a, int items_per_slot, cudaStream_t s) {
+static sf_status mr_once(const MrArgs &a, int items_per_slot, StatusPeek *peek, int64_t *ws_bytes,
+                         cudaStream_t s) {
     Scratch sc(s);
     MrBuffers b;
     b.cnt = sc.get<uint32_t>(a.ntiles);
@@ -1173,7 +1187,15 @@ static sf_status mr_once(const MrArgs &a, int items_per_slot, cudaStream_t s) {
     b.tot = sc.get<uint32_t>(4);
     SF_TRY_SCRATCH(sc);
     uint32_t total = 0;
-    SF_TRY((mr_count<KER, BW, CLIP, TZ>(a, b.cnt, b.off, b.tot, &total, s)));
+    SF_TRY((mr_count<KER, BW, CLIP, TZ>(a, b.cnt, b.off, b.tot, &total, peek, s)));
+    if (ws_bytes) {
+        int64_t slots = 0, max_items = 0;
+        uint32_t lpw = 0;
+        SF_TRY((mr_sizes<KER, BW, CLIP, false, TZ>(a, total, items_per_slot, &slots, &lpw, &max_items)));
+        *ws_bytes = 2 * scratch_round(4 * (int64_t)a.ntiles) + scratch_round(16) +
+                    mr_plan_bytes<TZ>(a.ntiles, total, max_items) + scan_parts_bytes_(a.ntiles);
+        return SF_OK;
+    }
     if (a.pairs) {
         SF_TRY((mr_plan<KER, BW, CLIP, true, TZ>(a, total, items_per_slot, b, &sc, nullptr, s)));
         SF_TRY_SCRATCH(sc);
@@ -1185,14 +1207,15 @@ static sf_status mr_once(const MrArgs &a, int items_per_slot, cudaStream_t s) {
 }
 
 template <int KER, int TZ>
-static sf_status dispatch_once(int bw, bool clip, const MrArgs &a, int ips, cudaStream_t s) {
+static sf_status dispatch_once(int bw, bool clip, const MrArgs &a, int ips, StatusPeek *pk,
+                               int64_t *ws, cudaStream_t s) {
     switch (bw * 2 + (clip ? 1 : 0)) {
-        case BW_ISO * 2 + 0: return mr_once<KER, BW_ISO, false, TZ>(a, ips, s);
-        case BW_ISO * 2 + 1: return mr_once<KER, BW_ISO, true, TZ>(a, ips, s);
-        case BW_UNIFORM * 2 + 0: return mr_once<KER, BW_UNIFORM, false, TZ>(a, ips, s);
-        case BW_UNIFORM * 2 + 1: return mr_once<KER, BW_UNIFORM, true, TZ>(a, ips, s);
-        case BW_ANISO * 2 + 0: return mr_once<KER, BW_ANISO, false, TZ>(a, ips, s);
-        default: return mr_once<KER, BW_ANISO, true, TZ>(a, ips, s);
+        case BW_ISO * 2 + 0: return mr_once<KER, BW_ISO, false, TZ>(a, ips, pk, ws, s);
+        case BW_ISO * 2 + 1: return mr_once<KER, BW_ISO, true, TZ>(a, ips, pk, ws, s);
+        case BW_UNIFORM * 2 + 0: return mr_once<KER, BW_UNIFORM, false, TZ>(a, ips, pk, ws, s);
+        case BW_UNIFORM * 2 + 1: return mr_once<KER, BW_UNIFORM, true, TZ>(a, ips, pk, ws, s);
+        case BW_ANISO * 2 + 0: return mr_once<KER, BW_ANISO, false, TZ>(a, ips, pk, ws, s);
+        default: return mr_once<KER, BW_ANISO, true, TZ>(a, ips, pk, ws, s);
     }
 }
 
@@ -1245,9 +1268,10 @@ static RoiDesc roi_desc(const GridSpec &g, int tz, const float2 *axis, int tile_
     return r;
 }
 
-sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
-                       const DensityCall &call, float *d_out, double *d_mass, cudaStream_t s,
-                       unsigned long long *d_pairs) {
+static sf_status density_grid_impl(sf_index *idx, const sf_box &roi, const GridSpec &g,
+                                   const DensityCall &call, float *d_out, double *d_mass,
+                                   cudaStream_t s, unsigned long long *d_pairs, StatusPeek *peek,
+                                   int64_t *ws_bytes) {
     constexpr int TZ = kTileZ;
     std::vector<float2> ax((size_t)g.nx + g.ny + g.nz);
     node_axes(g, ax.data());
@@ -1274,9 +1298,14 @@ sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
     {
         KTimer t(d_pairs ? "k_grid_count" : "k_grid", s);
         if (call.kernel == SF_K_EPAN)
-            SF_TRY((dispatch_once<SF_K_EPAN, TZ>(call.bw, call.clip != 0, a, 4, s)));
+            SF_TRY((dispatch_once<SF_K_EPAN, TZ>(call.bw, call.clip != 0, a, 4, peek, ws_bytes, s)));
         else
-            SF_TRY((dispatch_once<SF_K_GAUSS3, TZ>(call.bw, call.clip != 0, a, 4, s)));
+            SF_TRY((dispatch_once<SF_K_GAUSS3, TZ>(call.bw, call.clip != 0, a, 4, peek, ws_bytes, s)));
+    }
+    if (ws_bytes) {  // this function's own buffers on top of the execution's
+        *ws_bytes += scratch_round(sizeof(float2) * ax.size()) + scratch_round(8 * tiles) +
+                     scratch_round(sizeof(RoiDesc)) + scratch_round(4 * tiles);
+        return SF_OK;
     }
     if (d_mass) {
         const double cell = g.s[0] * g.s[1] * g.s[2];
@@ -1284,6 +1313,20 @@ sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
                            tiles, cell, d_mass));
     }
     return SF_OK;
+}
+
+sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
+                       const DensityCall &call, float *d_out, double *d_mass, cudaStream_t s,
+                       unsigned long long *d_pairs, StatusPeek *peek) {
+    return density_grid_impl(idx, roi, g, call, d_out, d_mass, s, d_pairs, peek, nullptr);
+}
+
+// Device bytes density_grid holds at its peak for this ROI (it runs the
+// candidate count, which synchronises the stream).
+sf_status grid_workspace(sf_index *idx, const sf_box &roi, const GridSpec &g,
+                         const DensityCall &call, int64_t *bytes, cudaStream_t s) {
+    *bytes = 0;
+    return density_grid_impl(idx, roi, g, call, nullptr, nullptr, s, nullptr, nullptr, bytes);
 }
 
 // Same result as density_grid with the monolithic kernel, on node coordinates
@@ -1337,7 +1380,7 @@ struct BatchPlan {
 template <int KER, int BW, bool CLIP, int TZ>
 static sf_status batch_build(BatchPlan &P, cudaStream_t s) {
     uint32_t total = 0;
-    SF_TRY((mr_count<KER, BW, CLIP, TZ>(P.a, P.b.cnt, P.b.off, P.b.tot, &total, s)));
+    SF_TRY((mr_count<KER, BW, CLIP, TZ>(P.a, P.b.cnt, P.b.off, P.b.tot, &total, nullptr, s)));
     SF_TRY((mr_plan<KER, BW, CLIP, false, TZ>(P.a, total, P.ips, P.b, nullptr, &P.owned, s)));
     if (!P.use_graph) return SF_OK;
     // capture the execution once, on a private stream (the caller's may be the
@@ -1513,8 +1556,10 @@ constexpr int kPtWarps = 4;
 
 struct PointsArgs {
     EngineArgs e;
-    float *rho_sorted;
-    uint8_t *inroi;
+    const int *leaves;          // query leaves (null: every leaf, slot = leaf)
+    int64_t nslots;             // number of query leaves
+    float *rho_sorted;          // [nslots * 32]: density of slot point (slot * 32 + lane)
+    uint8_t *inroi;             // [nslots * 32]: 1 if that point lies in the ROI
     unsigned long long *pairs;  // counting variant
 };
 
@@ -1548,16 +1593,18 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
     }
     __syncthreads();
     PtWarpSmem &S = W[warp];
-    const int64_t leaf = (int64_t)blockIdx.x * kPtWarps + warp;
-    if (leaf >= a.e.tv.cnt[0]) return;
+    const int64_t slot = (int64_t)blockIdx.x * kPtWarps + warp;
+    if (slot >= a.nslots) return;
+    const int64_t leaf = a.leaves ? (int64_t)a.leaves[slot] : slot;
     const int64_t qi = leaf * kLeaf + lane;
+    const int64_t oi = slot * kLeaf + lane;
     const bool valid = qi < a.e.tv.n;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) q = __ldg(&a.e.tv.pos[qi]);
     // query points: those inside the ROI box (closed)
     const bool active = valid && q.x >= a.e.blo[0] && q.x <= a.e.bhi[0] && q.y >= a.e.blo[1] &&
                         q.y <= a.e.bhi[1] && q.z >= a.e.blo[2] && q.z <= a.e.bhi[2];
-    if (valid) a.inroi[qi] = active ? 1 : 0;
+    a.inroi[oi] = active ? 1 : 0;
     const unsigned am = __ballot_sync(0xffffffffu, active);
     if (am == 0) return;
     float tlo[3] = {active ? q.x : INFINITY, active ? q.y : INFINITY, active ? q.z : INFINITY};
@@ -1720,7 +1767,7 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points(PointsArgs a) {
         if (CNT && (cnt & 1)) --npairs;  // the padding entry is "in support" (q = 0)
         add(a0 + a1);
     }
-    if (active) a.rho_sorted[qi] = (float)(((double)sum + (double)cmp) * s_inv);
+    if (active) a.rho_sorted[oi] = (float)(((double)sum + (double)cmp) * s_inv);
     if (CNT) {
         if (!active) npairs = 0;
 #pragma unroll
@@ -1833,15 +1880,17 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points_tc(PointsArgs a) {
     if (threadIdx.x == 0) s_inv = a.e.dp->inv_neff;
     __syncthreads();
     TcWarpSmem &S = W[warp];
-    const int64_t leaf = (int64_t)blockIdx.x * kPtWarps + warp;
-    if (leaf >= a.e.tv.cnt[0]) return;
+    const int64_t slot = (int64_t)blockIdx.x * kPtWarps + warp;
+    if (slot >= a.nslots) return;
+    const int64_t leaf = a.leaves ? (int64_t)a.leaves[slot] : slot;
     const int64_t qi = leaf * kLeaf + lane;
+    const int64_t oi = slot * kLeaf + lane;
     const bool valid = qi < a.e.tv.n;
     float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) q = __ldg(&a.e.tv.pos[qi]);
     const bool active = valid && q.x >= a.e.blo[0] && q.x <= a.e.bhi[0] && q.y >= a.e.blo[1] &&
                         q.y <= a.e.bhi[1] && q.z >= a.e.blo[2] && q.z <= a.e.bhi[2];
-    if (valid) a.inroi[qi] = active ? 1 : 0;
+    a.inroi[oi] = active ? 1 : 0;
     const unsigned am = __ballot_sync(0xffffffffu, active);
     if (am == 0) return;
     float tlo[3] = {active ? q.x : INFINITY, active ? q.y : INFINITY, active ? q.z : INFINITY};
@@ -1980,7 +2029,7 @@ __global__ void __launch_bounds__(kPtWarps * 32) k_points_tc(PointsArgs a) {
         const double t = __shfl_sync(0xffffffffu, v[sl], src);
         if (sl == mysl) mine = t;
     }
-    if (active) a.rho_sorted[qi] = (float)(mine * s_inv);
+    if (active) a.rho_sorted[oi] = (float)(mine * s_inv);
 }
 
 template <int KER, bool CLIP>
@@ -1997,15 +2046,18 @@ static cudaError_t launch_points_tc(int prec, const PointsArgs &a, int64_t nleaf
 }
 
 sf_status density_points_tc(sf_index *idx, const sf_box &roi, const DensityCall &call, int prec,
-                            float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s) {
+                            const int *d_leaves, int64_t nslots, float *d_rho_sorted,
+                            uint8_t *d_inroi, cudaStream_t s) {
     if (call.bw != BW_ISO)
         return fail(SF_ERR_INVALID_ARG, "tensor-core point densities need isotropic (kNN) bandwidths");
     PointsArgs a;
     a.e = engine_args(idx, roi, call);
+    a.leaves = d_leaves;
+    a.nslots = d_leaves ? nslots : idx->cnt[0];
     a.rho_sorted = d_rho_sorted;
     a.inroi = d_inroi;
     a.pairs = nullptr;
-    const int64_t nl = idx->cnt[0];
+    const int64_t nl = a.nslots;
     cudaError_t e;
     if (call.kernel == SF_K_EPAN)
         e = call.clip ? launch_points_tc<SF_K_EPAN, true>(prec, a, nl, s) : launch_points_tc<SF_K_EPAN, false>(prec, a, nl, s);
@@ -2016,16 +2068,18 @@ sf_status density_points_tc(sf_index *idx, const sf_box &roi, const DensityCall 
 }
 
 sf_status density_points(sf_index *idx, const sf_box &roi, const DensityCall &call,
-                         float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s,
-                         unsigned long long *d_pairs) {
+                         const int *d_leaves, int64_t nslots, float *d_rho_sorted,
+                         uint8_t *d_inroi, cudaStream_t s, unsigned long long *d_pairs) {
     PointsArgs a;
     a.e = engine_args(idx, roi, call);
+    a.leaves = d_leaves;
+    a.nslots = d_leaves ? nslots : idx->cnt[0];
     a.rho_sorted = d_rho_sorted;
     a.inroi = d_inroi;
     a.pairs = d_pairs;
     cudaError_t e = (call.kernel == SF_K_EPAN)
-                        ? dispatch_points<SF_K_EPAN>(call.bw, call.clip != 0, a, idx->cnt[0], s)
-                        : dispatch_points<SF_K_GAUSS3>(call.bw, call.clip != 0, a, idx->cnt[0], s);
+                        ? dispatch_points<SF_K_EPAN>(call.bw, call.clip != 0, a, a.nslots, s)
+                        : dispatch_points<SF_K_GAUSS3>(call.bw, call.clip != 0, a, a.nslots, s);
     SF_TRY_CUDA(e);
     return SF_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -61,17 +62,52 @@ inline unsigned blocks_for(int64_t n, int per_block) {
     return (unsigned)((n + per_block - 1) / per_block);
 }
 
+// Raise a kernel's dynamic shared-memory limit once per device (the attribute
+// is per device; the flag word is per kernel, one bit per device ordinal < 64).
+template <typename K>
+inline cudaError_t smem_attr_once(K kernel, size_t smem, std::atomic<uint64_t> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
+
+// A device status word to read back at a synchronisation the call makes anyway
+// (the copy is queued just before that synchronisation).
+struct StatusPeek {
+    const int *d_src = nullptr;  // per-call device status word (ST_*)
+    int value = 0;               // host copy, valid after the synchronisation
+};
+
 // ---------------------------------------------------------------------------
 // Stream-ordered scratch memory (cudaMallocAsync from the device's default
 // pool, released at scope exit with cudaFreeAsync on the same stream).
 // ---------------------------------------------------------------------------
+// Bytes of scratch the calling thread holds, and the most it has held since the
+// start of its current library call (each allocation counted rounded up to 256 B).
+struct ScratchStats {
+    int64_t live = 0;
+    int64_t peak = 0;
+};
+ScratchStats &scratch_stats();  // thread-local
+constexpr int64_t kScratchAlign = 256;
+inline int64_t scratch_round(int64_t bytes) {
+    return (std::max<int64_t>(bytes, 1) + kScratchAlign - 1) / kScratchAlign * kScratchAlign;
+}
+
 struct Scratch {
     cudaStream_t s;
     std::vector<void *> ptrs;
+    int64_t held = 0;
     cudaError_t err = cudaSuccess;
     explicit Scratch(cudaStream_t st) : s(st) {}
     ~Scratch() {
         for (void *p : ptrs) cudaFreeAsync(p, s);
+        scratch_stats().live -= held;
     }
     template <typename T>
     T *get(int64_t count) {
@@ -83,6 +119,11 @@ struct Scratch {
             return nullptr;
         }
         ptrs.push_back(p);
+        const int64_t b = scratch_round(count * (int64_t)sizeof(T));
+        held += b;
+        ScratchStats &st = scratch_stats();
+        st.live += b;
+        if (st.live > st.peak) st.peak = st.live;
         return static_cast<T *>(p);
     }
 };
@@ -239,6 +280,17 @@ struct GridSpec {
     double lo[3], hi[3], s[3];
 };
 
+// Count the points of a sorted cloud inside [lo, hi] (closed, float bounds) into *cnt.
+__global__ void k_count_box(const float4 *__restrict__ pos, int64_t n, float3 lo, float3 hi,
+                            unsigned long long *cnt);
+// N_eff = *cnt (clip scope) or n_all (cnt == NULL), 1/N_eff and the uniform lengths
+// into *dp; ST_EMPTY into *status (nullable) when N_eff = 0.
+__global__ void k_set_params(DensityParams *dp, const unsigned long long *cnt, int64_t n_all,
+                             float ex, float ey, float ez, int *status);
+// Launches the two above for one ROI; d_status (nullable) is the call's own status word.
+sf_status set_density_params(sf_index *idx, bool clip, const sf_box &roi, const float ell[3],
+                             DensityParams *d_dp, int *d_status, cudaStream_t s);
+
 struct DensityCall {
     int kernel;       // SF_K_*
     int bw;           // BwMode
@@ -248,15 +300,22 @@ struct DensityCall {
     float4 *nell_override;     // node max-ell array to use (null: the index's own)
 };
 
+// peek (nullable): a status word read back at the call's sizing synchronisation.
 sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,
                        const DensityCall &call, float *d_out, double *d_mass, cudaStream_t s,
-                       unsigned long long *d_pairs = nullptr);
+                       unsigned long long *d_pairs = nullptr, StatusPeek *peek = nullptr);
 
-// Density at the sorted points inside roi (DIRECT). d_rho_sorted[i] for sorted
-// i in roi, d_inroi[i] = 1/0. d_count receives the number of roi points.
+// Density (DIRECT) at the points of the query leaves d_leaves[0..nslots) that lie
+// inside roi: for slot t and lane l (the point of sorted index d_leaves[t] * 32 + l),
+// d_inroi[t * 32 + l] = 1/0 and, if 1, d_rho_sorted[t * 32 + l] = its density.
+// d_leaves == NULL: every leaf in order (slot = leaf; nslots ignored).
 sf_status density_points(sf_index *idx, const sf_box &roi, const DensityCall &call,
-                         float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s,
-                         unsigned long long *d_pairs = nullptr);
+                         const int *d_leaves, int64_t nslots, float *d_rho_sorted,
+                         uint8_t *d_inroi, cudaStream_t s, unsigned long long *d_pairs = nullptr);
+// The same with the tensor-core cross term (prec = SF_PREC_TF32 / 3XTF32 / BF16).
+sf_status density_points_tc(sf_index *idx, const sf_box &roi, const DensityCall &call, int prec,
+                            const int *d_leaves, int64_t nslots, float *d_rho_sorted,
+                            uint8_t *d_inroi, cudaStream_t s);
 
 // Node max smoothing length per axis for BW_ISO (from pos.w) or BW_ANISO (from ell,
 // only points inside roi when clip) into d_nell.

@@ -631,11 +631,8 @@ sf_status knn_run(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_sorted,
     a.h_sorted = d_h_sorted;
     a.nbr_orig = d_nbr_orig;
     const size_t smem = sizeof(KnnWarpSmem) * kKnnWarps;
-    static bool attr = false;
-    if (!attr) {
-        SF_TRY_CUDA(cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    SF_TRY_CUDA(smem_attr_once(k_knn, smem, attr));
     int dev = 0, sms = 0, per_sm = 0;
     SF_TRY_CUDA(cudaGetDevice(&dev));
     SF_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

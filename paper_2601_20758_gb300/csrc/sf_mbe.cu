@@ -17,9 +17,6 @@
 
 namespace sf {
 
-sf_status set_density_params(sf_index *idx, bool clip, const sf_box &roi, const float ell[3],
-                             DensityParams *d_dp, cudaStream_t s);
-
 struct InterpGrid {
     int nx, ny, nz;
     double lo[3], inv_s[3];
@@ -144,16 +141,21 @@ __global__ void k_asl(const uint32_t *__restrict__ list, int64_t m, const float 
     }
 }
 
-__global__ void k_interp(const float4 *__restrict__ pos, int64_t n, float3 lo, float3 hi,
-                         const float *__restrict__ grid, InterpGrid g, float *__restrict__ rho,
-                         uint8_t *__restrict__ inroi) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+// Slot i = t * 32 + l is the point of sorted index leaves[t] * 32 + l.
+__global__ void k_interp(const float4 *__restrict__ pos, int64_t n, const int *__restrict__ leaves,
+                         int64_t nslots, float3 lo, float3 hi, const float *__restrict__ grid,
+                         InterpGrid g, float *__restrict__ rho, uint8_t *__restrict__ inroi) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslots * kLeaf;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 p = pos[i];
-        const bool in = p.x >= lo.x && p.x <= hi.x && p.y >= lo.y && p.y <= hi.y && p.z >= lo.z &&
-                        p.z <= hi.z;
+        const int64_t j = (int64_t)leaves[i / kLeaf] * kLeaf + (i % kLeaf);
+        bool in = false;
+        if (j < n) {
+            const float4 p = pos[j];
+            in = p.x >= lo.x && p.x <= hi.x && p.y >= lo.y && p.y <= hi.y && p.z >= lo.z &&
+                 p.z <= hi.z;
+            if (in) rho[i] = trilinear(grid, g, p.x, p.y, p.z);
+        }
         inroi[i] = in ? 1 : 0;
-        if (in) rho[i] = trilinear(grid, g, p.x, p.y, p.z);
     }
 }
 
@@ -245,7 +247,8 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
     float *pilot = d_pilot_out ? d_pilot_out : sc.get<float>(G);
     SF_TRY_SCRATCH(sc);
     const float ellf[3] = {(float)ell0[0], (float)ell0[1], (float)ell0[2]};
-    SF_TRY(set_density_params(idx, true, roi, ellf, d_dp, s));
+    // N_B >= 2 here, so the scope is never empty: no status word is needed
+    SF_TRY(set_density_params(idx, true, roi, ellf, d_dp, nullptr, s));
     DensityCall pc;
     pc.kernel = kernel;
     pc.bw = BW_UNIFORM;
@@ -275,11 +278,13 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
 }
 
 sf_status interp_points(sf_index *idx, const sf_box &roi, const GridSpec &g, const float *d_grid,
-                        float *d_rho_sorted, uint8_t *d_inroi, cudaStream_t s) {
+                        const int *d_leaves, int64_t nslots, float *d_rho_sorted, uint8_t *d_inroi,
+                        cudaStream_t s) {
     float3 lo, hi;
     box_bounds(roi, lo, hi);
-    SF_TRY_CUDA(launch(k_interp, dim3(sgrid(idx->n)), dim3(256), 0, s, (const float4 *)idx->pos,
-                       idx->n, lo, hi, d_grid, interp_grid(g), d_rho_sorted, d_inroi));
+    SF_TRY_CUDA(launch(k_interp, dim3(sgrid(nslots * kLeaf)), dim3(256), 0, s,
+                       (const float4 *)idx->pos, idx->n, d_leaves, nslots, lo, hi, d_grid,
+                       interp_grid(g), d_rho_sorted, d_inroi));
     return SF_OK;
 }
 

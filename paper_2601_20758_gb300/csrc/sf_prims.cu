@@ -23,8 +23,20 @@ sf_status fail(sf_status st, const char *fmt, ...) {
     return st;
 }
 
+static thread_local ScratchStats t_scratch;
+
+ScratchStats &scratch_stats() { return t_scratch; }
+
 const char *last_error_cstr() { return t_last_error.c_str(); }
-void clear_error() { t_last_error.clear(); }
+
+// Every entry point starts here: the error message and the scratch high-water
+// mark of the previous call are closed.
+void clear_error() {
+    t_last_error.clear();
+    t_scratch.peak = t_scratch.live;
+}
+
+int64_t last_call_scratch_peak() { return t_scratch.peak; }
 
 // ---------------------------------------------------------------------------
 // Kernel timing registry: event pairs recorded on the launching stream.

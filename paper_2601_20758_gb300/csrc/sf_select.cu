@@ -1,6 +1,5 @@
 // sf_select.cu -- density-threshold selection (Sec. 4.1: a density threshold
-// decides which points are selected) and the ROI point compaction that puts
-// per-point densities in ascending original-index order.
+// decides which points are selected).
 //
 // The nearest-rank threshold is an exact order statistic of the float32
 // densities, found by radix selection on their bit patterns (integer work,
@@ -89,60 +88,6 @@ sf_status select_points(const float *d_density, const uint32_t *d_ids, int64_t n
         if (h_nsel) *h_nsel = ht;
         if (h_threshold) *h_threshold = tv;
     }
-    return SF_OK;
-}
-
-// ---------------------------------------------------------------------------
-// ROI point densities, sorted order -> ascending original index
-// ---------------------------------------------------------------------------
-__global__ void k_to_orig(const uint8_t *__restrict__ inroi, const float *__restrict__ rho,
-                          const uint32_t *__restrict__ perm, int64_t n,
-                          uint32_t *__restrict__ flag_o, float *__restrict__ rho_o) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t o = perm[i];
-        const bool in = inroi[i] != 0;
-        flag_o[o] = in ? 1u : 0u;
-        if (in) rho_o[o] = rho[i];
-    }
-}
-
-__global__ void k_compact_orig(const uint32_t *__restrict__ flag_o, const uint32_t *__restrict__ pos,
-                               const float *__restrict__ rho_o, int64_t n, float *__restrict__ dens,
-                               uint32_t *__restrict__ ids) {
-    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n;
-         o += (int64_t)gridDim.x * blockDim.x) {
-        if (flag_o[o]) {
-            const uint32_t p = pos[o];
-            dens[p] = rho_o[o];
-            ids[p] = (uint32_t)o;
-        }
-    }
-}
-
-sf_status compact_roi_points(sf_index *idx, const uint8_t *d_inroi, const float *d_rho_sorted,
-                             float *d_density, uint32_t *d_ids, int64_t capacity,
-                             int64_t *h_count, cudaStream_t s) {
-    const int64_t n = idx->n;
-    Scratch sc(s);
-    uint32_t *flag_o = sc.get<uint32_t>(n);
-    uint32_t *pos = sc.get<uint32_t>(n);
-    float *rho_o = sc.get<float>(n);
-    uint32_t *total = sc.get<uint32_t>(1);
-    SF_TRY_SCRATCH(sc);
-    SF_TRY_CUDA(launch(k_to_orig, dim3(stride_grid(n)), dim3(256), 0, s, d_inroi, d_rho_sorted,
-                       (const uint32_t *)idx->perm, n, flag_o, rho_o));
-    SF_TRY(scan_u32(flag_o, pos, n, total, s));
-    uint32_t ht = 0;
-    SF_TRY_CUDA(cudaMemcpyAsync(&ht, total, sizeof ht, cudaMemcpyDeviceToHost, s));
-    SF_TRY_CUDA(cudaStreamSynchronize(s));
-    *h_count = ht;
-    if ((int64_t)ht > capacity)
-        return fail(SF_ERR_CAPACITY, "sf_kde_points: %u ROI points exceed capacity %lld", ht,
-                    (long long)capacity);
-    SF_TRY_CUDA(launch(k_compact_orig, dim3(stride_grid(n)), dim3(256), 0, s,
-                       (const uint32_t *)flag_o, (const uint32_t *)pos, (const float *)rho_o, n,
-                       d_density, d_ids));
     return SF_OK;
 }
 

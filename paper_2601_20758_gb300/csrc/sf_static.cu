@@ -31,6 +31,7 @@ struct StaticScratch {
     float2 axis[3 * kStaticMaxDim];     // node coordinates, (hi, lo) float pairs
     DensityParams dp;                   // N_eff and the fixed lengths
     unsigned long long count;           // particles in the ROI (clip scope)
+    int status;                         // this call's status word (ST_EMPTY)
     double mass;                        // FP64 total mass
     double mass_part[kStaticMaxTiles];  // per-tile partial sums
 };
@@ -56,6 +57,15 @@ sf_status static_scratch(StaticScratch **out) {
     SF_TRY_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(SF_ERR_INVALID_ARG, "device ordinal %d", dev);
     std::lock_guard<std::mutex> lk(g_static_mu);
+    if (g_static_addr[dev]) {
+        // a context torn down since (cudaDeviceReset) leaves a stale address: check it
+        cudaPointerAttributes at;
+        const cudaError_t e = cudaPointerGetAttributes(&at, g_static_addr[dev]);
+        if (e != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != dev) {
+            (void)cudaGetLastError();  // the query's error must not surface at the next launch
+            g_static_addr[dev] = nullptr;
+        }
+    }
     if (!g_static_addr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
@@ -87,31 +97,6 @@ __global__ void k_static_axis(float2 *axis, int nx, int ny, int nz, double3 lo, 
     const double r = __dadd_rn(l, __dmul_rn((double)i, sp));
     const float h = (float)r;
     axis[t] = make_float2(h, (float)__dsub_rn(r, (double)h));
-}
-
-__global__ void k_static_count(const float4 *__restrict__ pos, int64_t n, float3 lo, float3 hi,
-                               unsigned long long *cnt) {
-    unsigned long long c = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 p = pos[i];
-        c += (p.x >= lo.x && p.x <= hi.x && p.y >= lo.y && p.y <= hi.y && p.z >= lo.z && p.z <= hi.z);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
-}
-
-__global__ void k_static_params(DensityParams *dp, const unsigned long long *cnt, int clip,
-                                int64_t n_all, float ex, float ey, float ez, int *status) {
-    const int64_t neff = clip ? (int64_t)*cnt : n_all;
-    dp->ell_uniform[0] = ex;
-    dp->ell_uniform[1] = ey;
-    dp->ell_uniform[2] = ez;
-    dp->pad0 = 0.f;
-    dp->neff = neff;
-    dp->inv_neff = neff > 0 ? 1.0 / (double)neff : 0.0;
-    if (neff == 0 && status) *status = ST_EMPTY;
 }
 
 }  // namespace sf
@@ -185,13 +170,15 @@ extern "C" sf_status sf_kde_grid_static(sf_index *idx, const sf_box *roi, const 
         // the count is left over from the previous call: clear it first
         SF_TRY_CUDA(cudaMemsetAsync(&S->count, 0, sizeof(unsigned long long), s));
         const unsigned gb = std::max(1u, std::min<unsigned>(blocks_for(idx->n, 256), 152 * 8));
-        SF_TRY_CUDA(launch(k_static_count, dim3(gb), dim3(256), 0, s, (const float4 *)idx->pos, idx->n,
+        SF_TRY_CUDA(launch(k_count_box, dim3(gb), dim3(256), 0, s, (const float4 *)idx->pos, idx->n,
                            make_float3(lo[0], lo[1], lo[2]), make_float3(hi[0], hi[1], hi[2]),
                            &S->count));
     }
-    SF_TRY_CUDA(launch(k_static_params, dim3(1), dim3(1), 0, s, &S->dp,
-                       (const unsigned long long *)&S->count, clip ? 1 : 0, idx->n, ell[0], ell[1],
-                       ell[2], idx->d_status));
+    // so is the status word
+    SF_TRY_CUDA(cudaMemsetAsync(&S->status, 0, sizeof(int), s));
+    SF_TRY_CUDA(launch(k_set_params, dim3(1), dim3(1), 0, s, &S->dp,
+                       clip ? (const unsigned long long *)&S->count : nullptr, idx->n, ell[0],
+                       ell[1], ell[2], &S->status));
     SF_TRY_CUDA(launch(k_static_axis, dim3(blocks_for(g.nx + g.ny + g.nz, 256)), dim3(256), 0, s,
                        S->axis, g.nx, g.ny, g.nz, make_double3(g.lo[0], g.lo[1], g.lo[2]),
                        make_double3(g.s[0], g.s[1], g.s[2])));
@@ -205,8 +192,13 @@ extern "C" sf_status sf_kde_grid_static(sf_index *idx, const sf_box *roi, const 
     SF_TRY(density_grid_prealloc(idx, *roi, g, call, S->axis, S->mass_part, d_out,
                                  h_mass ? &S->mass : nullptr, s));
     if (h_mass) {
+        // the status is read only here, where the call synchronises anyway
+        int st = 0;
         SF_TRY_CUDA(cudaMemcpyAsync(h_mass, &S->mass, sizeof(double), cudaMemcpyDeviceToHost, s));
-        return sf_sync_status(idx, stream);
+        SF_TRY_CUDA(cudaMemcpyAsync(&st, &S->status, sizeof st, cudaMemcpyDeviceToHost, s));
+        SF_TRY_CUDA(cudaStreamSynchronize(s));
+        if (st == ST_EMPTY)
+            return fail(SF_ERR_EMPTY_ROI, "sf_kde_grid_static: no particle of the scope lies in the ROI");
     }
     return SF_OK;
 }

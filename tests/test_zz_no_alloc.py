@@ -11,6 +11,9 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
+from tests.parity import density_check
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -31,11 +34,11 @@ def L():
     return _lib
 
 
-def _static(L, idx, box, dims, kernel, p, out):
+def _static(L, idx, box, dims, kernel, p, out, want_mass=True):
     d = (ctypes.c_int32 * 3)(*dims)
     m = ctypes.c_double(0.0)
     st = L.load().sf_kde_grid_static(idx, ctypes.byref(box), d, kernel, ctypes.byref(p),
-                                     out.data_ptr(), ctypes.byref(m), None)
+                                     out.data_ptr(), ctypes.byref(m) if want_mass else None, None)
     return st, m.value
 
 
@@ -78,5 +81,51 @@ def test_static_grid_rejects_sizes_beyond_its_scratch(L):
         assert st == L.SF_ERR_INVALID_ARG and "static scratch" in L.sf_last_error()
         st, _ = _static(L, idx, L.make_box((0, 0, 0), (1, 1, 1)), (1024, 1024, 1024), L.SF_K_EPAN, p, out)
         assert st == L.SF_ERR_INVALID_ARG and "static scratch" in L.sf_last_error()
+    finally:
+        L.sf_free_index(idx)
+
+
+def test_static_grid_against_oracle_and_shrinking_clip_rois(L):
+    """The allocation-free kernel against the FP64 oracle directly, and the shared
+    scratch starting clean on every call: a clip-scope kNN ROI followed by one that
+    holds fewer points (the point count is cleared, not carried over), a call without
+    the mass on an empty clip ROI (zero grid, no error reported, nothing left behind),
+    and a normal call after it."""
+    from paper_2601_20758_gb300 import synth
+    xyz = synth.plain_cloud(6000, seed=12)
+    n = xyz.shape[0]
+    d = torch.from_numpy(xyz).cuda()
+    idx = L.sf_build_index(d)
+    try:
+        pk = L.make_params(rule=L.SF_BW_KNN, k=16, scope=L.SF_SCOPE_CLIP)
+        L.sf_bandwidths(idx, pk)
+        h = torch.empty(n, device="cuda")
+        L.sf_get_bandwidths(idx, h)
+        ell = oracle.iso_ell(h.cpu().numpy())
+        rois = [((0.1, 0.1, 0.1), (0.9, 0.9, 0.9)), ((0.3, 0.35, 0.4), (0.6, 0.55, 0.7))]
+        dims = (21, 18, 13)
+        G = dims[0] * dims[1] * dims[2]
+        for kernel, okern in ((L.SF_K_GAUSS3, oracle.GAUSS3), (L.SF_K_EPAN, oracle.EPAN)):
+            for lo, hi in rois:             # the second ROI holds fewer points
+                out = torch.full((G,), -1.0, device="cuda")
+                st, m = _static(L, idx, L.make_box(lo, hi), dims, kernel, pk, out)
+                assert st == L.SF_OK, L.sf_last_error()
+                mem = oracle.in_box(xyz, (lo, hi))
+                ref = oracle.density_at(xyz, ell, oracle.grid_nodes((lo, hi), dims), okern,
+                                        1.0 / int(mem.sum()), member=mem)
+                density_check(out.cpu().numpy(), ref, label=f"static k{kernel} {lo}")
+                alloc = torch.empty(G, device="cuda")
+                L.sf_kde_grid(idx, L.make_box(lo, hi), dims, kernel, pk, alloc)
+                np.testing.assert_allclose(out.cpu().numpy(), alloc.cpu().numpy(), rtol=1e-5,
+                                           atol=1e-5 * float(alloc.abs().max()))
+        far = L.make_box((5, 5, 5), (6, 6, 6))
+        out = torch.full((G,), 3.0, device="cuda")
+        st, _ = _static(L, idx, far, dims, L.SF_K_GAUSS3, pk, out, want_mass=False)
+        assert st == L.SF_OK, L.sf_last_error()
+        torch.cuda.synchronize()
+        assert float(out.abs().max()) == 0.0
+        assert L.sf_sync_status(idx) == L.SF_OK
+        st, m = _static(L, idx, L.make_box(*rois[1]), dims, L.SF_K_GAUSS3, pk, out)
+        assert st == L.SF_OK and m > 0.0, L.sf_last_error()
     finally:
         L.sf_free_index(idx)
