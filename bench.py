@@ -1,24 +1,33 @@
 #!/usr/bin/env python
-"""Benchmark: on-the-fly adaptive KDE recompute over nested ROIs of a 16M-point
-cosmology-shaped cloud, through the C ABI of libscalefree.so.
+"""Benchmark: on-the-fly adaptive KDE recompute over zoom ROIs of a 1.07B-point
+cloud on one GB300, through the C ABI of libscalefree.so.
 
-One step = the whole hot path over one cloud:
-  index build (Morton sort + nodes) -> kNN bandwidths (k = 64) -> for each of 5
-  nested cubic ROIs (edge 4^-i, centred on the densest 1/256 cell): density on a
-  128^3 grid (truncated Gaussian, 3h), density at every ROI point (direct sums),
-  selection of the points above the 90th density percentile.
+Default workload (large-1.07B): 1,073,741,824 float32 points (Soneira-Peebles
+hierarchical clustering + 10,000 NFW halos) drawn on the device; the index and
+the k = 64 kNN bandwidths are built once and stay resident in HBM (timed apart
+as "setup"). One step = the recompute of the 8 zoom ROIs (edge 10^(-3i/7),
+around the most massive halo) as 256^3 density grids (truncated Gaussian, 3h,
+global scope), one sf_kde_grid per ROI on one stream.
 
-value = in-support kernel evaluations per second (the (target, particle) pairs
+value = in-support kernel evaluations per second (the (node, particle) pairs
 with a non-zero kernel, counted once by the library's counting variant before
-timing), whole job, inputs resident in HBM. Per-ROI recompute latencies
-(grid + points + selection) are reported as p50 / p99 beside it.
+timing), whole job, index resident in HBM. Per-ROI recompute latencies are
+reported as p50 / p99 against the 11.1 ms (90 Hz) frame budget.
+
+Nested in the same line:
+  cosmology_16M  the 16.8M-point cosmology step (index + kNN + 5 nested ROIs at
+                 128^3 + point densities + 90th-percentile selection per step),
+                 the batched 64-ROI case and the tensor-core precision variants;
+  serving        a Poisson stream of navigation recomputes over the resident
+                 1.07B-point index, 70% FP32 / 30% BF16 requests.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config large|cosmology]
 
---impl reference times the FP64 oracle (brute force, OpenMP) on a bounded
-sample of the same workload on the host cores. N > 1 (torchrun): every rank is
-an independent replica of the whole step (no data-path collective); value sums
-all ranks' work over the slowest rank's time.
+--impl reference times the FP64 oracle (brute force, OpenMP) on a bounded sample
+of the same workload on the host cores. N > 1 (torchrun): every rank is an
+independent replica of the whole step (no data-path collective); value sums all
+ranks' work over the slowest rank's time.
 """
 import argparse
 import ctypes
@@ -38,18 +47,28 @@ if ROOT not in sys.path:
 
 METRIC = "ROI density recompute p50/p99 ms and kernel evals/s; HBM fraction vs oracle at 1e-5"
 UNIT = "kernel evals/s"
-N_POINTS = 16_777_216
 K_NN = 64
-DIMS = (128, 128, 128)
-N_ROI = 5
-PCT = 90.0
-WORKLOAD = ("cosmology-16M: 16,777,216 float32 points (80% Soneira-Peebles eta=4 lambda=1.9 "
-            "12 levels + 20% uniform, periodic unit box), k=64 kNN bandwidths, truncated "
-            "Gaussian kernel (3h), global scope, 5 nested cubic ROIs (edge 4^-i) at 128^3, "
-            "direct point densities in each ROI, selection above the 90th percentile")
+BUDGET_MS = 11.1
 # algorithmic FP32 operations of one truncated-Gaussian pair evaluation:
 # 3 differences, 3 scalings by 1/h, 3 squares + 2 adds, 1 multiply-add into the sum
 FLOPS_PER_PAIR = 13
+
+LARGE_N = 1 << 30
+LARGE_DIMS = (256, 256, 256)
+LARGE_ROIS = 8
+LARGE_WORKLOAD = ("large-1.07B: 1,073,741,824 float32 points (80% Soneira-Peebles eta=4 lambda=1.9 "
+                  "12 levels + 20% in 10,000 NFW halos, c in [5, 15], masses over 3 decades), k=64 "
+                  "kNN bandwidths resident, truncated Gaussian (3h), global scope, 8 zoom ROIs (edge "
+                  "10^(-3i/7)) centred on the most massive halo at 256^3; one step = the 8 ROI grids")
+
+COSMO_N = 16_777_216
+COSMO_DIMS = (128, 128, 128)
+COSMO_ROIS = 5
+PCT = 90.0
+COSMO_WORKLOAD = ("cosmology-16M: 16,777,216 float32 points (80% Soneira-Peebles eta=4 lambda=1.9 "
+                  "12 levels + 20% uniform, periodic unit box), k=64 kNN bandwidths, truncated "
+                  "Gaussian kernel (3h), global scope, 5 nested cubic ROIs (edge 4^-i) at 128^3, "
+                  "direct point densities in each ROI, selection above the 90th percentile")
 
 
 def parse():
@@ -58,19 +77,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="cosmology", choices=["cosmology", "large"],
-                    help="cosmology: the 16.8M-point benchmark step; large: the 1.07B-point "
-                         "cloud with 8 zoom ROIs at 256^3 (ROI grid recompute latency)")
+    ap.add_argument("--config", default="large", choices=["large", "cosmology"],
+                    help="large: the 1.07B-point cloud, 8 zoom ROIs at 256^3 (default); "
+                         "cosmology: the 16.8M-point step alone")
+    ap.add_argument("--points", type=int, default=0,
+                    help="cloud size override (smaller clouds are for profiling only, not bench lines)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--points", type=int, default=N_POINTS,
-                    help="cloud size (smaller clouds are for profiling only, not bench lines)")
-    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop sample")
+    ap.add_argument("--no-nested", action="store_true", help="skip the nested 16.8M-point legs")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-vs-plain comparison over 64 uneven ROIs")
     ap.add_argument("--no-prec", action="store_true",
                     help="skip the tensor-core precision variants of the point densities")
-    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-slots", type=int, default=4, help="concurrent requests (streams)")
     ap.add_argument("--no-count", action="store_true",
                     help="skip the pair-counting pass (value and roofline become null)")
@@ -84,13 +105,20 @@ def dist_setup(ngpus):
     return rank, world, local
 
 
-def make_workload(n_points=N_POINTS):
+def cosmology_workload(n_points=COSMO_N):
     import numpy as np
     from paper_2601_20758_gb300 import synth
     xyz = synth.cosmology_cloud(n_points)
     centre = synth.densest_cell_centre(xyz, 256)
-    rois = synth.nested_rois(centre, N_ROI, 4.0)
+    rois = synth.nested_rois(centre, COSMO_ROIS, 4.0)
     return np.ascontiguousarray(xyz), rois
+
+
+def large_workload(n_points=LARGE_N):
+    """The 1.07B-point cloud on the device (seeded, counter-based generator) and its ROIs."""
+    from paper_2601_20758_gb300 import synth
+    d_xyz, centre = synth.large_cloud_device(n_points)
+    return d_xyz, synth.zoom_rois(centre, LARGE_ROIS, 3.0)
 
 
 # ---------------------------------------------------------------------------
@@ -150,52 +178,73 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (the cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(xyz, rois, n_knn=256, n_vox=512, seed=5):
+def oracle_sample(xyz, roi, dims, n_knn, n_vox, seed=5, stride=1):
     """Brute-force FP64 oracle on a bounded sample of the workload.
 
-    kNN (k=64) of n_knn sampled points over all N, then the truncated-Gaussian
-    density at n_vox sampled nodes of the first (full-cube) ROI grid over all N
-    points, with the bandwidth set to the median of the sampled kNN distances.
+    kNN (k=64) of n_knn sampled points over the cloud (every `stride`-th point of it),
+    then the truncated-Gaussian density at n_vox sampled nodes of the ROI grid over
+    those points, with the bandwidth set to the median of the sampled kNN distances.
     Returns (in-support pairs evaluated, wall seconds, threads, description)."""
     import numpy as np
     import oracle
     rng = np.random.default_rng(seed)
-    q = np.sort(rng.choice(xyz.shape[0], n_knn, replace=False))
+    if stride > 1:
+        xyz = np.ascontiguousarray(xyz[::stride])
+    n = xyz.shape[0]
+    q = np.sort(rng.choice(n, n_knn, replace=False))
     t0 = time.perf_counter()
     h, _, _ = oracle.knn(xyz, K_NN, queries=q)
     hmed = float(np.median(h))
-    nodes = oracle.grid_nodes(rois[0], DIMS)
-    v = nodes[np.sort(rng.choice(nodes.shape[0], n_vox, replace=False))]
-    ell = np.broadcast_to(np.array([hmed, hmed, hmed]), (xyz.shape[0], 3))
-    out = oracle.density_at(xyz, np.ascontiguousarray(ell), v, oracle.GAUSS3, 1.0 / xyz.shape[0])
+    (ax, ay, az), _ = oracle.grid_axes(roi, dims)
+    flat = np.sort(rng.choice(dims[0] * dims[1] * dims[2], n_vox, replace=False))
+    ix, iy, iz = flat % dims[0], (flat // dims[0]) % dims[1], flat // (dims[0] * dims[1])
+    v = np.ascontiguousarray(np.stack([ax[ix], ay[iy], az[iz]], axis=1))
+    ell = np.broadcast_to(np.array([hmed, hmed, hmed]), (n, 3))
+    out = oracle.density_at(xyz, np.ascontiguousarray(ell), v, oracle.GAUSS3, 1.0 / n)
     dt = time.perf_counter() - t0
     pairs = int(out["pairs"].sum()) + n_knn * K_NN
-    desc = (f"FP64 brute force over all {xyz.shape[0]} points: kNN (k={K_NN}) of {n_knn} sampled "
-            f"points + truncated-Gaussian density at {n_vox} sampled nodes of the full-cube 128^3 "
-            f"grid with the sampled median kNN bandwidth; value = in-support pairs found / wall time")
+    over = f"all {n} points" if stride == 1 else f"{n} points (every {stride}th of the cloud)"
+    desc = (f"FP64 brute force over {over}: kNN (k={K_NN}) of {n_knn} sampled points + "
+            f"truncated-Gaussian density at {n_vox} sampled nodes of the full-cube "
+            f"{dims[0]}^3 grid with the sampled median kNN bandwidth; value = in-support pairs "
+            f"found / wall time")
     return pairs, dt, oracle.num_threads(), desc
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores over a bounded sample of the same workload,
+    per step (rank 0 only)."""
     if rank != 0:
         return 0
-    import numpy as np  # noqa: F401
-    xyz, rois = make_workload()
+    if args.config == "large":
+        import torch
+        n = args.points or LARGE_N
+        d_xyz, rois = large_workload(n)       # the seeded input generator (device), not timed
+        xyz = d_xyz.cpu().numpy()
+        del d_xyz
+        roi, dims, nk, nv, stride, workload = rois[0], LARGE_DIMS, 8, 8, 16, LARGE_WORKLOAD
+        torch.cuda.empty_cache()
+    else:
+        xyz, rois = cosmology_workload(args.points or COSMO_N)
+        roi, dims, nk, nv, stride, workload = rois[0], COSMO_DIMS, 256, 512, 1, COSMO_WORKLOAD
     for _ in range(args.warmup):
-        oracle_sample(xyz, rois)
+        oracle_sample(xyz, roi, dims, nk, nv, stride=stride)
     tot_pairs, tot_t = 0, 0.0
+    desc, thr = "", 0
     for _ in range(args.steps):
-        p, dt, thr, desc = oracle_sample(xyz, rois)
+        p, dt, thr, desc = oracle_sample(xyz, roi, dims, nk, nv, stride=stride)
         tot_pairs += p
         tot_t += dt
     val = tot_pairs / tot_t
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": desc},
+            "data": "synthetic", "config": {"workload": workload, "sample": desc},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -203,318 +252,8 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
-# Our arm
+# helpers
 # ---------------------------------------------------------------------------
-def main():
-    args = parse()
-    rank, world, local = dist_setup(args.gpus)
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
-    if args.config == "large":
-        return run_large(args, rank, world, local)
-    import numpy as np
-    import torch
-    import torch.distributed as dist
-    from paper_2601_20758_gb300 import build
-    from paper_2601_20758_gb300 import _lib as L
-
-    build.build()
-    L.load()
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    stream = torch.cuda.current_stream()
-    xyz, rois = make_workload(args.points)
-    n = xyz.shape[0]
-    d_xyz = torch.from_numpy(xyz).cuda()
-    p = L.make_params(rule=L.SF_BW_KNN, k=K_NN, scope=L.SF_SCOPE_GLOBAL)
-    boxes = [L.make_box(lo, hi) for lo, hi in rois]
-    G = DIMS[0] * DIMS[1] * DIMS[2]
-    grids = [torch.empty(G, dtype=torch.float32, device="cuda") for _ in rois]
-    dens = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in rois]
-    ids = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in rois]
-    masks = [torch.empty(n, dtype=torch.uint8, device="cuda") for _ in rois]
-    sels = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in rois]
-
-    # algorithmic work: in-support pairs per ROI, counted once (not timed)
-    pairs_grid, pairs_pts = [], []
-    if not args.no_count:
-        idx = L.sf_build_index(d_xyz, stream)
-        L.sf_bandwidths(idx, p, stream)
-    for b in ([] if args.no_count else boxes):
-        gp, pp = ctypes.c_int64(0), ctypes.c_int64(0)
-        dims = (ctypes.c_int32 * 3)(*DIMS)
-        st = L.load().sf_count_support_pairs(idx, ctypes.byref(b), dims, L.SF_K_GAUSS3,
-                                             ctypes.byref(p), ctypes.byref(gp), ctypes.byref(pp),
-                                             L._stream(stream))
-        L._check("sf_count_support_pairs", st)
-        pairs_grid.append(gp.value)
-        pairs_pts.append(pp.value)
-    if not args.no_count:
-        L.sf_free_index(idx)
-    pairs_step = sum(pairs_grid) + sum(pairs_pts)
-
-    roi_ms = []
-    ev_roi = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in rois]
-
-    def step(record_roi=False, counts=None):
-        idx = L.sf_build_index(d_xyz, stream)
-        try:
-            L.sf_bandwidths(idx, p, stream)
-            for i, b in enumerate(boxes):
-                if record_roi:
-                    ev_roi[i][0].record(stream)
-                L.sf_kde_grid(idx, b, DIMS, L.SF_K_GAUSS3, p, grids[i], stream=stream)
-                cnt = L.sf_kde_points(idx, b, None, L.SF_K_GAUSS3, p, dens[i], ids[i], stream=stream)
-                nsel, _ = L.sf_select(idx, dens[i], ids[i], cnt, n, math.nan, PCT, masks[i], sels[i],
-                                      stream=stream)
-                if record_roi:
-                    ev_roi[i][1].record(stream)
-                if counts is not None:
-                    counts.append((cnt, nsel))
-        finally:
-            L.sf_free_index(idx)
-        if record_roi:
-            torch.cuda.synchronize()
-            roi_ms.extend(a.elapsed_time(z) for a, z in ev_roi)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    # ---- device-resident timed region
-    L.load().sf_kernel_timing_enable(1)
-    L.load().sf_kernel_timing_reset()
-    sampler = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    launches0 = L.sf_launch_count()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for _ in range(args.steps):
-        step(record_roi=True)
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    launches = L.sf_launch_count() - launches0
-    clocks = sampler.stop()
-    L.load().sf_kernel_timing_enable(0)
-    elapsed_ms = t_start.elapsed_time(t_end)
-    # per-kernel device time on the launching stream
-    kern = {}
-    for name in ("k_points", "k_grid", "k_knn", "k_radix_sort"):
-        ms, cnt = ctypes.c_double(0), ctypes.c_int64(0)
-        L._check("sf_kernel_timing", L.load().sf_kernel_timing(name.encode(), ctypes.byref(ms), ctypes.byref(cnt)))
-        kern[name] = {"ms_total": ms.value, "launches": cnt.value}
-        if name in ("k_points", "k_grid") and hasattr(L.load(), "sf_kernel_timing_list"):
-            arr = (ctypes.c_double * 4096)()
-            got = ctypes.c_int64(0)
-            L._check("sf_kernel_timing_list", L.load().sf_kernel_timing_list(
-                name.encode(), arr, 4096, ctypes.byref(got)))
-            per = [arr[i] for i in range(min(got.value, 4096))]
-            # launches per step are one per ROI: average each ROI over the timed steps
-            kern[name]["per_roi_ms"] = [sum(per[r::N_ROI]) / max(1, len(per[r::N_ROI]))
-                                        for r in range(N_ROI)] if len(per) >= N_ROI else per
-    L.load().sf_kernel_timing_reset()
-    elapsed_ms = slowest_rank(elapsed_ms, world, dist, "cuda")
-    ms_per_step = elapsed_ms / args.steps
-    value = whole_job_rate(pairs_step * args.steps, world, elapsed_ms / 1e3) if pairs_step else None
-
-    # ---- roofline of the dominant kernel
-    dom = max(kern, key=lambda k: kern[k]["ms_total"])
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peaks = {}
-    if os.path.exists(peaks_path):
-        with open(peaks_path) as fh:
-            peaks = json.load(fh)
-    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-    kd = kern[dom]
-    avg_ms = kd["ms_total"] / max(kd["launches"], 1)
-    if dom == "k_points":
-        work = sum(pairs_pts) * FLOPS_PER_PAIR / N_ROI
-        roof = {"kernel": dom, "bound": "alu", "achieved": work / (avg_ms * 1e-3) / 1e12,
-                "peak": fp32_peak_tflops, "unit": "TFLOP/s"}
-    elif dom == "k_grid":
-        work = sum(pairs_grid) * FLOPS_PER_PAIR / N_ROI
-        roof = {"kernel": dom, "bound": "alu", "achieved": work / (avg_ms * 1e-3) / 1e12,
-                "peak": fp32_peak_tflops, "unit": "TFLOP/s"}
-    else:
-        # kNN: compulsory bytes per point, 16 B read (the sorted point) + 4 B written (h);
-        # radix sort: 8 passes of 8-bit digits, each reading and writing 12 B per point
-        byts = n * 20 if dom == "k_knn" else n * 8 * 24
-        roof = {"kernel": dom, "bound": "hbm", "achieved": byts / (avg_ms * 1e-3) / 1e9,
-                "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s"}
-    if not pairs_step and roof["bound"] == "alu":
-        roof["achieved"] = None
-    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] is not None else None
-    roof["peak_source"] = ("FP32 lanes x 2 x max SM clock of measured peaks file"
-                           if roof["bound"] == "alu" else "measured HBM copy bandwidth")
-    roof["traffic"] = load_traffic(dom)
-    roof["avg_launch_ms"] = avg_ms
-
-    # ---- end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(args, L, torch, xyz, boxes, p, pairs_step, stream, world, barrier, dist)
-
-    # ---- serving loop: Poisson navigation stream over the resident index
-    serving = None
-    if not args.no_serve:
-        serving = run_serving(args, L, torch, d_xyz, p, rois)
-
-    # ---- 64 uneven ROIs: one graph-captured persistent execution vs 64 plain calls
-    batched = None
-    if not args.no_batch:
-        batched = run_batched(args, L, torch, d_xyz, p, stream)
-
-    # ---- tensor-core precision variants of the point densities (ROI 1)
-    precision = None
-    if not args.no_prec:
-        precision = run_precision(L, torch, d_xyz, p, boxes[1], stream)
-
-    # ---- CPU baseline (rank 0, N = 1 only)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        pr, dt, thr, desc = oracle_sample(xyz, rois)
-        cpu = {"value": pr / dt, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
-               "seconds": dt}
-
-    if rank == 0:
-        roi_sorted = sorted(roi_ms)
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD if n == N_POINTS else f"{n}-point variant (profiling only)",
-                           "points": n, "k": K_NN, "grid": list(DIMS),
-                           "rois": N_ROI, "roi_edges": [float(hi[0] - lo[0]) for lo, hi in rois],
-                           "l2": "inputs larger than L2 (256 MB sorted points, 5 x 8 MB grids)",
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roi_recompute_ms": {"p50": percentile(roi_sorted, 50), "p99": percentile(roi_sorted, 99),
-                                     "n": len(roi_sorted), "budget_ms": 11.1},
-                "pairs_per_step": {"grid": pairs_grid, "points": pairs_pts},
-                "kernels_ms_per_step": {k: v["ms_total"] / args.steps for k, v in kern.items()},
-                "kernels_ms_per_roi": {k: v.get("per_roi_ms") for k, v in kern.items() if "per_roi_ms" in v},
-                "serving": serving,
-                "batched": batched,
-                "precision": precision,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks}
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
-
-
-LARGE_N = 1 << 30
-LARGE_DIMS = (256, 256, 256)
-LARGE_WORKLOAD = ("large-1.07B: 1,073,741,824 float32 points (80% Soneira-Peebles eta=4 lambda=1.9 "
-                  "12 levels + 20% in 10,000 NFW halos, c in [5, 15], masses over 3 decades), k=64 "
-                  "kNN bandwidths resident, truncated Gaussian, global scope, 8 zoom ROIs (edge "
-                  "10^(-3i/7)) centred on the most massive halo at 256^3; one step = the 8 ROI grids")
-
-
-def run_large(args, rank, world, local):
-    """ROI grid recompute on the 1.07B-point cloud: the cloud is drawn on the device,
-    the index and the kNN bandwidths are built once (timed, reported apart), then
-    every step recomputes the 8 zoom ROIs' 256^3 grids; per-ROI latency from CUDA
-    events on the launching stream."""
-    import torch
-    from paper_2601_20758_gb300 import build, synth
-    from paper_2601_20758_gb300 import _lib as L
-    build.build()
-    L.load()
-    torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream()
-    n = args.points if args.points != N_POINTS else LARGE_N
-    t0 = time.perf_counter()
-    d_xyz, centre = synth.large_cloud_device(n)
-    torch.cuda.synchronize()
-    gen_s = time.perf_counter() - t0
-    rois = synth.zoom_rois(centre, 8, 3.0)
-    boxes = [L.make_box(lo, hi) for lo, hi in rois]
-    p = L.make_params(rule=L.SF_BW_KNN, k=K_NN, scope=L.SF_SCOPE_GLOBAL)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    ev[0].record(stream)
-    idx = L.sf_build_index(d_xyz, stream)
-    ev[1].record(stream)
-    L.sf_bandwidths(idx, p, stream)
-    ev[2].record(stream)
-    torch.cuda.synchronize()
-    build_ms, bw_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-    del d_xyz
-    torch.cuda.empty_cache()
-    try:
-        G = LARGE_DIMS[0] * LARGE_DIMS[1] * LARGE_DIMS[2]
-        grids = [torch.empty(G, device="cuda") for _ in rois]
-        pairs = []
-        if not args.no_count:
-            for b in boxes:
-                gp = ctypes.c_int64(0)
-                dims = (ctypes.c_int32 * 3)(*LARGE_DIMS)
-                L._check("sf_count_support_pairs", L.load().sf_count_support_pairs(
-                    idx, ctypes.byref(b), dims, L.SF_K_GAUSS3, ctypes.byref(p), ctypes.byref(gp),
-                    None, L._stream(stream)))
-                pairs.append(gp.value)
-        ev_roi = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in rois]
-
-        def step(record):
-            for i, b in enumerate(boxes):
-                if record:
-                    ev_roi[i][0].record(stream)
-                L.sf_kde_grid(idx, b, LARGE_DIMS, L.SF_K_GAUSS3, p, grids[i], stream=stream)
-                if record:
-                    ev_roi[i][1].record(stream)
-
-        for _ in range(args.warmup):
-            step(False)
-        torch.cuda.synchronize()
-        sampler = ClockSampler(local)
-        sampler.start()
-        launches0 = L.sf_launch_count()
-        roi_ms = [[] for _ in rois]
-        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            step(True)
-            torch.cuda.synchronize()
-            for i in range(len(rois)):
-                roi_ms[i].append(ev_roi[i][0].elapsed_time(ev_roi[i][1]))
-        z.record(stream)
-        torch.cuda.synchronize()
-        clocks = sampler.stop()
-        launches = L.sf_launch_count() - launches0
-        total_ms = a.elapsed_time(z)
-    finally:
-        L.sf_free_index(idx)
-    flat = sorted(x for r in roi_ms for x in r)
-    ms_step = total_ms / args.steps
-    line = {"metric": METRIC, "value": (sum(pairs) * args.steps / (total_ms / 1e3)) if pairs else None,
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": LARGE_WORKLOAD if n == LARGE_N else f"{n}-point variant of the large cloud",
-                       "points": n, "k": K_NN, "grid": list(LARGE_DIMS), "rois": len(rois),
-                       "roi_edges": [float(hi[0] - lo[0]) for lo, hi in rois],
-                       "l2": "inputs larger than L2 (17 GB sorted points)", "parallelism": "single GPU"},
-            "roi_recompute_ms": {"p50": percentile(flat, 50), "p99": percentile(flat, 99), "n": len(flat),
-                                 "budget_ms": 11.1,
-                                 "per_roi_median": [sorted(r)[len(r) // 2] for r in roi_ms]},
-            "pairs_per_step": {"grid": pairs},
-            "setup": {"cloud_generation_s": gen_s, "index_build_ms": build_ms, "bandwidths_ms": bw_ms},
-            "gpu_launches": launches, "clocks": clocks}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
-
-
 def slowest_rank(elapsed, world, dist, device):
     """The max over ranks of a timing (every rank gets it)."""
     if world <= 1:
@@ -559,38 +298,449 @@ def load_traffic(kernel):
         return None
 
 
-def run_serving(args, L, torch, d_xyz, p, rois):
-    """Continuous admission of ROI recomputes (grid + point densities + selection)
-    arriving as a Poisson stream (mean 200/s) that walks zoom and pan over three
-    decades of scale with grid edges 64..256, on --serve-slots slots (streams)."""
-    from paper_2601_20758_gb300 import serve
-    n = d_xyz.shape[0]
-    idx = L.sf_build_index(d_xyz)
+def peaks(torch, local):
+    """Roofline denominators: the measured HBM copy bandwidth, and the FP32 FMA rate
+    (SMs x 128 lanes x 2 flops x the maximum SM clock of the measured peaks file)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    pk = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            pk = json.load(fh)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    return {"hbm_gbs": pk.get("hbm_gbs", 6800.0), "fp32_tflops": sms * 128 * 2 * mhz * 1e6 / 1e12,
+            "hbm_source": "measured HBM copy bandwidth" if "hbm_gbs" in pk else "fallback 6.8 TB/s",
+            "fp32_source": "FP32 lanes x 2 x max SM clock of the measured peaks file"}
+
+
+def kernel_times(L, names, per_launch=False):
+    """Per-name CUDA-event totals (ms, launches) recorded on the launching streams."""
+    out = {}
+    for name in names:
+        ms, cnt = ctypes.c_double(0), ctypes.c_int64(0)
+        L._check("sf_kernel_timing", L.load().sf_kernel_timing(name.encode(), ctypes.byref(ms),
+                                                               ctypes.byref(cnt)))
+        ent = {"ms_total": ms.value, "launches": cnt.value}
+        if per_launch and cnt.value:
+            arr = (ctypes.c_double * 8192)()
+            got = ctypes.c_int64(0)
+            L._check("sf_kernel_timing_list", L.load().sf_kernel_timing_list(
+                name.encode(), arr, 8192, ctypes.byref(got)))
+            ent["list"] = [arr[i] for i in range(min(got.value, 8192))]
+        out[name] = ent
+    return out
+
+
+def count_pairs(L, idx, boxes, dims, p, stream, points=False):
+    grid_pairs, point_pairs = [], []
+    for b in boxes:
+        gp, pp = ctypes.c_int64(0), ctypes.c_int64(0)
+        d = (ctypes.c_int32 * 3)(*dims)
+        L._check("sf_count_support_pairs", L.load().sf_count_support_pairs(
+            idx, ctypes.byref(b), d, L.SF_K_GAUSS3, ctypes.byref(p), ctypes.byref(gp),
+            ctypes.byref(pp) if points else None, L._stream(stream)))
+        grid_pairs.append(gp.value)
+        point_pairs.append(pp.value)
+    return grid_pairs, point_pairs
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    import torch.distributed as dist
+    from paper_2601_20758_gb300 import build
+    from paper_2601_20758_gb300 import _lib as L
+    build.build()
+    L.load()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ctx = {"args": args, "L": L, "torch": torch, "dist": dist, "rank": rank, "world": world,
+           "local": local, "barrier": barrier, "stream": torch.cuda.current_stream()}
+    if args.config == "cosmology":
+        line = run_cosmology(ctx, nested=False)
+    else:
+        line = run_large(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def timed_steps(ctx, step, n_rois, steps):
+    """Run `steps` steps between a barrier + device synchronisation on both sides,
+    CUDA events on the launching stream around the whole region and around every
+    ROI; nvidia-smi samples the clocks meanwhile. Returns (elapsed ms (max over
+    ranks), per-ROI ms lists, clocks, launches)."""
+    torch, L, stream = ctx["torch"], ctx["L"], ctx["stream"]
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(n_rois)] for _ in range(steps)]
+    sampler = ClockSampler(ctx["local"])
+    ctx["barrier"]()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = L.sf_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(steps):
+        step(ev[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    ctx["barrier"]()
+    launches = L.sf_launch_count() - launches0
+    clocks = sampler.stop()
+    elapsed = slowest_rank(t_start.elapsed_time(t_end), ctx["world"], ctx["dist"], "cuda")
+    roi_ms = [[ev[s][r][0].elapsed_time(ev[s][r][1]) for s in range(steps)] for r in range(n_rois)]
+    return elapsed, roi_ms, clocks, launches
+
+
+def run_large(ctx):
+    """The 1.07B-point configuration: cloud drawn on the device, index and kNN
+    bandwidths built once (timed apart), then every step recomputes the 8 zoom
+    ROIs' 256^3 grids; per-ROI latency from CUDA events on the launching stream."""
+    args, L, torch, stream = ctx["args"], ctx["L"], ctx["torch"], ctx["stream"]
+    rank, world = ctx["rank"], ctx["world"]
+    n = args.points or LARGE_N
+    t0 = time.perf_counter()
+    d_xyz, rois = large_workload(n)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    boxes = [L.make_box(lo, hi) for lo, hi in rois]
+    p = L.make_params(rule=L.SF_BW_KNN, k=K_NN, scope=L.SF_SCOPE_GLOBAL)
+    lib = L.load()
+    lib.sf_kernel_timing_enable(1)
+    lib.sf_kernel_timing_reset()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    idx = L.sf_build_index(d_xyz, stream)
+    ev[1].record(stream)
+    L.sf_bandwidths(idx, p, stream)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    setup_kern = kernel_times(L, ("k_knn", "k_radix_sort"))
+    lib.sf_kernel_timing_reset()
+    lib.sf_kernel_timing_enable(0)
+    pk = peaks(torch, ctx["local"])
+    knn_ms = setup_kern["k_knn"]["ms_total"]
+    setup = {"cloud_generation_s": gen_s, "index_build_ms": ev[0].elapsed_time(ev[1]),
+             "bandwidths_ms": ev[1].elapsed_time(ev[2]),
+             "k_knn_ms": knn_ms, "k_radix_sort_ms": setup_kern["k_radix_sort"]["ms_total"],
+             # kNN: compulsory bytes per point, 16 B read (the sorted point) + 4 B written (h)
+             "k_knn_hbm_frac": (n * 20 / (knn_ms * 1e-3) / 1e9) / pk["hbm_gbs"] if knn_ms else None,
+             "k_knn_queries_per_s": n / (knn_ms * 1e-3) if knn_ms else None}
+    xyz_host = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        xyz_host = d_xyz.cpu().numpy()
+    del d_xyz
+    torch.cuda.empty_cache()
     try:
-        L.sf_bandwidths(idx, p)
-        centre = [(float(rois[-1][0][k]) + float(rois[-1][1][k])) / 2 for k in range(3)]
-        reqs = serve.navigation_requests(args.serve_requests, rate=200.0, centre=centre, seed=2601,
-                                         select_every=10)
-        free, _ = torch.cuda.mem_get_info()
-        slots = args.serve_slots
-        ex = serve.GpuExecutor(idx, p, L.SF_K_GAUSS3, n, slots=slots, max_nodes=256 ** 3)
-        srv = serve.Server(ex, slots=slots, mem_budget=int(0.5 * free), n_points=n)
-        try:
-            # warm the slots once (first-use costs), then replay the stream
-            warm = [serve.Request(-1 - i, r.lo, r.hi, r.dims) for i, r in enumerate(reqs[:slots])]
-            srv.replay(warm)
-            srv.completed.clear()
-            st = srv.replay(reqs)
-        finally:
-            srv.close()
-        st["rate_per_s"] = 200.0
-        st["stream"] = ("Poisson arrivals, zoom walk over log10 edge in [-3, 0] (sigma 0.1 decade), "
-                        "pan <= half an edge, grid edge in {64, 96, 128, 192, 256}^3; every request "
-                        "recomputes the ROI grid, every 10th also the ROI point densities and the "
-                        "90th-percentile selection")
-        return st
+        G = LARGE_DIMS[0] * LARGE_DIMS[1] * LARGE_DIMS[2]
+        grids = [torch.empty(G, device="cuda") for _ in rois]
+        pairs = [] if args.no_count else count_pairs(L, idx, boxes, LARGE_DIMS, p, stream)[0]
+        work_counts = [] if args.no_count else [
+            L.sf_grid_work_counts(idx, b, LARGE_DIMS, L.SF_K_GAUSS3, p, stream) for b in boxes]
+
+        def step(evs=None):
+            for i, b in enumerate(boxes):
+                if evs:
+                    evs[i][0].record(stream)
+                L.sf_kde_grid(idx, b, LARGE_DIMS, L.SF_K_GAUSS3, p, grids[i], stream=stream)
+                if evs:
+                    evs[i][1].record(stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        lib.sf_kernel_timing_enable(1)
+        lib.sf_kernel_timing_reset()
+        elapsed, roi_ms, clocks, launches = timed_steps(ctx, step, len(rois), args.steps)
+        kern = kernel_times(L, ("k_grid", "k_grid_work"), per_launch=True)
+        lib.sf_kernel_timing_enable(0)
+        lib.sf_kernel_timing_reset()
+        ms_step = elapsed / args.steps
+        value = whole_job_rate(sum(pairs) * args.steps, world, elapsed / 1e3) if pairs else None
+
+        # roofline of the dominant kernel: the grid's persistent work kernel
+        work = kern["k_grid_work"]
+        wl = work["list"]
+        per_roi_work = [statistics.median(wl[r::len(rois)]) for r in range(len(rois))] if wl else []
+        avg_ms = work["ms_total"] / max(work["launches"], 1)
+        achieved = (sum(pairs) * FLOPS_PER_PAIR / len(rois)) / (avg_ms * 1e-3) / 1e12 if pairs else None
+        roof = {"kernel": "k_mr_work", "bound": "alu", "achieved": achieved, "peak": pk["fp32_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"] if achieved else None,
+                "traffic": load_traffic("k_mr_work"), "avg_launch_ms": avg_ms,
+                "peak_source": pk["fp32_source"],
+                "work_unit": f"{FLOPS_PER_PAIR} FP32 flops per in-support (node, particle) pair"}
+
+        flat = sorted(x for r in roi_ms for x in r)
+        e2e = None if args.no_e2e else run_e2e_large(ctx, idx, boxes, p, grids, sum(pairs))
+        serving = None if args.no_serve else run_serving(ctx, idx, n, p, rois)
     finally:
         L.sf_free_index(idx)
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if xyz_host is not None:
+        pr, dt, thr, desc = oracle_sample(xyz_host, rois[0], LARGE_DIMS, 16, 32, stride=16)
+        cpu = {"value": pr / dt, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
+               "seconds": dt}
+        del xyz_host
+    nested = None if args.no_nested else run_cosmology(ctx, nested=True)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": LARGE_WORKLOAD if n == LARGE_N else f"{n}-point variant (profiling only)",
+                       "points": n, "k": K_NN, "grid": list(LARGE_DIMS), "rois": len(rois),
+                       "roi_edges": [float(hi[0] - lo[0]) for lo, hi in rois],
+                       "l2": "inputs larger than L2 (17 GB sorted points, 8 x 67 MB grids)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roi_recompute_ms": {"p50": percentile(flat, 50), "p99": percentile(flat, 99),
+                                 "n": len(flat), "budget_ms": BUDGET_MS,
+                                 "per_roi_median": [statistics.median(r) for r in roi_ms],
+                                 "per_roi_max": [max(r) for r in roi_ms],
+                                 "within_budget": sum(x <= BUDGET_MS for x in flat)},
+            "pairs_per_step": {"grid": pairs},
+            "grid_work_per_roi": work_counts,
+            "kernels_ms_per_step": {"k_grid": kern["k_grid"]["ms_total"] / args.steps,
+                                    "k_grid_work": work["ms_total"] / args.steps},
+            "k_grid_work_ms_per_roi": per_roi_work,
+            "setup": setup, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks, "serving": serving,
+            "cosmology_16M": nested}
+
+
+def run_e2e_large(ctx, idx, boxes, p, grids, pairs_step):
+    """The same step through the C ABI with host buffers: every ROI grid is copied back
+    into pinned host memory inside the timed region (the index stays resident; the
+    step's inputs are the ROI boxes, passed from host memory)."""
+    args, L, torch, stream = ctx["args"], ctx["L"], ctx["torch"], ctx["stream"]
+    G = LARGE_DIMS[0] * LARGE_DIMS[1] * LARGE_DIMS[2]
+    h_grid = [torch.empty(G).pin_memory() for _ in boxes]
+
+    def step():
+        for i, b in enumerate(boxes):
+            L.sf_kde_grid(idx, b, LARGE_DIMS, L.SF_K_GAUSS3, p, grids[i], stream=stream)
+            h_grid[i].copy_(grids[i], non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    ctx["barrier"]()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    el = slowest_rank(time.perf_counter() - t0, ctx["world"], ctx["dist"], "cuda")
+    return {"value": whole_job_rate(pairs_step * args.steps, ctx["world"], el) if pairs_step else None,
+            "unit": UNIT, "h2d_bytes_per_step": len(boxes) * ctypes.sizeof(L.sf_box),
+            "d2h_bytes_per_step": len(boxes) * G * 4, "ms_per_step": 1e3 * el / args.steps}
+
+
+def run_serving(ctx, idx, n, p, rois):
+    """Continuous admission of ROI grid recomputes arriving as a Poisson stream that
+    walks zoom and pan over three decades of scale (grid edges 64..256) over the
+    resident index. Admission by the library's workspace figure."""
+    from paper_2601_20758_gb300 import serve
+    args, L, torch = ctx["args"], ctx["L"], ctx["torch"]
+    lo, hi = rois[-1]
+    centre = [(float(lo[k]) + float(hi[k])) / 2 for k in range(3)]
+    reqs = serve.navigation_requests(args.serve_requests, rate=args.serve_rate, centre=centre,
+                                     seed=2601)
+    free, _ = torch.cuda.mem_get_info()
+    slots = args.serve_slots
+    ex = serve.GpuExecutor(idx, p, L.SF_K_GAUSS3, n, slots=slots, max_nodes=256 ** 3, max_points=1)
+    srv = serve.Server(ex, slots=slots, mem_budget=int(0.5 * free))
+    try:
+        warm = [serve.Request(-1 - i, r.lo, r.hi, r.dims, want_points=r.want_points, prec=r.prec)
+                for i, r in enumerate(reqs[:2 * slots])]
+        srv.replay(warm)
+        srv.completed.clear()
+        st = srv.replay(reqs)
+    finally:
+        srv.close()
+    ok = [r for r in srv.completed if r.status == "done"]
+    st["service_p99_by_grid_edge_ms"] = {
+        str(e): percentile(sorted(1e3 * (r.done - r.admitted) for r in ok if r.dims[0] == e), 99)
+        for e in (64, 96, 128, 192, 256)}
+    st["rate_per_s"] = args.serve_rate
+    st["stream"] = ("Poisson arrivals over the 1.07B-point cloud, zoom walk over log10 edge in "
+                    "[-3, 0] (sigma 0.1 decade), pan <= half an edge, grid edge in "
+                    "{64, 96, 128, 192, 256}^3; every request recomputes the ROI grid (FP32)")
+    return st
+
+
+def run_cosmology(ctx, nested):
+    """The 16.8M-point cosmology step: index build -> kNN bandwidths (k = 64) -> for
+    each of 5 nested cubic ROIs (edge 4^-i, centred on the densest 1/256 cell):
+    density on a 128^3 grid, density at every ROI point, selection above the 90th
+    percentile. Nested in the default line it runs at most 5 timed steps and adds
+    the batched 64-ROI case and the precision variants; alone it is a full line."""
+    args, L, torch, stream = ctx["args"], ctx["L"], ctx["torch"], ctx["stream"]
+    rank, world = ctx["rank"], ctx["world"]
+    steps = min(args.steps, 5) if nested else args.steps
+    warmup = min(args.warmup, 3) if nested else args.warmup
+    xyz, rois = cosmology_workload(args.points if (args.points and not nested) else COSMO_N)
+    n = xyz.shape[0]
+    d_xyz = torch.from_numpy(xyz).cuda()
+    p = L.make_params(rule=L.SF_BW_KNN, k=K_NN, scope=L.SF_SCOPE_GLOBAL)
+    boxes = [L.make_box(lo, hi) for lo, hi in rois]
+    G = COSMO_DIMS[0] * COSMO_DIMS[1] * COSMO_DIMS[2]
+    grids = [torch.empty(G, dtype=torch.float32, device="cuda") for _ in rois]
+    dens = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in rois]
+    ids = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in rois]
+    masks = [torch.empty(n, dtype=torch.uint8, device="cuda") for _ in rois]
+    sels = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in rois]
+    pairs_grid, pairs_pts = [], []
+    if not args.no_count:
+        idx = L.sf_build_index(d_xyz, stream)
+        try:
+            L.sf_bandwidths(idx, p, stream)
+            pairs_grid, pairs_pts = count_pairs(L, idx, boxes, COSMO_DIMS, p, stream, points=True)
+        finally:
+            L.sf_free_index(idx)
+    pairs_step = sum(pairs_grid) + sum(pairs_pts)
+
+    def step(evs=None):
+        idx = L.sf_build_index(d_xyz, stream)
+        try:
+            L.sf_bandwidths(idx, p, stream)
+            for i, b in enumerate(boxes):
+                if evs:
+                    evs[i][0].record(stream)
+                L.sf_kde_grid(idx, b, COSMO_DIMS, L.SF_K_GAUSS3, p, grids[i], stream=stream)
+                cnt = L.sf_kde_points(idx, b, None, L.SF_K_GAUSS3, p, dens[i], ids[i], stream=stream)
+                L.sf_select(idx, dens[i], ids[i], cnt, n, math.nan, PCT, masks[i], sels[i], stream=stream)
+                if evs:
+                    evs[i][1].record(stream)
+        finally:
+            L.sf_free_index(idx)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    lib = L.load()
+    lib.sf_kernel_timing_enable(1)
+    lib.sf_kernel_timing_reset()
+    elapsed, roi_ms, clocks, launches = timed_steps(ctx, step, len(rois), steps)
+    kern = kernel_times(L, ("k_points", "k_grid", "k_grid_work", "k_knn", "k_radix_sort"))
+    lib.sf_kernel_timing_enable(0)
+    lib.sf_kernel_timing_reset()
+    ms_step = elapsed / steps
+    value = whole_job_rate(pairs_step * steps, world, elapsed / 1e3) if pairs_step else None
+    pk = peaks(torch, ctx["local"])
+    dom = max(("k_points", "k_grid", "k_knn", "k_radix_sort"), key=lambda k: kern[k]["ms_total"])
+    kd = kern[dom]
+    avg_ms = kd["ms_total"] / max(kd["launches"], 1)
+    if dom in ("k_points", "k_grid"):
+        work = sum(pairs_pts if dom == "k_points" else pairs_grid) * FLOPS_PER_PAIR / len(rois)
+        ach = work / (avg_ms * 1e-3) / 1e12 if pairs_step else None
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk["fp32_tflops"],
+                "unit": "TFLOP/s", "peak_source": pk["fp32_source"]}
+    else:
+        # kNN: compulsory 16 B read + 4 B written per point; radix sort: 8 passes x 24 B
+        byts = n * 20 if dom == "k_knn" else n * 8 * 24
+        roof = {"kernel": dom, "bound": "hbm", "achieved": byts / (avg_ms * 1e-3) / 1e9,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk["hbm_source"]}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] is not None else None
+    roof["traffic"] = load_traffic(dom)
+    roof["avg_launch_ms"] = avg_ms
+    flat = sorted(x for r in roi_ms for x in r)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": COSMO_WORKLOAD if n == COSMO_N else f"{n}-point variant (profiling only)",
+                      "points": n, "k": K_NN, "grid": list(COSMO_DIMS), "rois": len(rois),
+                      "roi_edges": [float(hi[0] - lo[0]) for lo, hi in rois],
+                      "l2": "inputs larger than L2 (256 MB sorted points, 5 x 8 MB grids)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "roi_recompute_ms": {"p50": percentile(flat, 50), "p99": percentile(flat, 99),
+                                "n": len(flat), "budget_ms": BUDGET_MS},
+           "pairs_per_step": {"grid": pairs_grid, "points": pairs_pts},
+           "kernels_ms_per_step": {k: v["ms_total"] / steps for k, v in kern.items()},
+           "roofline": roof, "gpu_launches": launches, "clocks": clocks}
+    if not args.no_batch:
+        out["batched"] = run_batched(args, L, torch, d_xyz, p, stream)
+    if not args.no_prec:
+        out["precision"] = run_precision(L, torch, d_xyz, p, boxes[1], stream)
+    if not nested:
+        out["e2e"] = None if args.no_e2e else run_e2e_cosmology(ctx, xyz, boxes, p, pairs_step)
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            pr, dt, thr, desc = oracle_sample(xyz, rois[0], COSMO_DIMS, 256, 512)
+            cpu = {"value": pr / dt, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
+                   "seconds": dt}
+        out["cpu_baseline"] = cpu
+    del d_xyz, grids, dens, ids, masks, sels
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_e2e_cosmology(ctx, xyz, boxes, p, pairs_step):
+    """The cosmology step with the cloud in pinned host memory and every result
+    (grids, point densities and ids, selections) copied back to the host."""
+    args, L, torch, stream = ctx["args"], ctx["L"], ctx["torch"], ctx["stream"]
+    n = xyz.shape[0]
+    h_xyz = torch.from_numpy(xyz).pin_memory()
+    d_xyz = torch.empty_like(h_xyz, device="cuda")
+    G = COSMO_DIMS[0] * COSMO_DIMS[1] * COSMO_DIMS[2]
+    grids = [torch.empty(G, device="cuda") for _ in boxes]
+    dens = [torch.empty(n, device="cuda") for _ in boxes]
+    ids = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in boxes]
+    sels = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in boxes]
+    h_grid = [torch.empty(G).pin_memory() for _ in boxes]
+    h_dens = [torch.empty(n).pin_memory() for _ in boxes]
+    h_ids = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in boxes]
+    h_sel = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in boxes]
+    stats = {"h2d": 0, "d2h": 0}
+
+    def step():
+        h2d = d2h = 0
+        d_xyz.copy_(h_xyz, non_blocking=True)
+        h2d += h_xyz.numel() * 4
+        idx = L.sf_build_index(d_xyz, stream)
+        try:
+            L.sf_bandwidths(idx, p, stream)
+            for i, b in enumerate(boxes):
+                L.sf_kde_grid(idx, b, COSMO_DIMS, L.SF_K_GAUSS3, p, grids[i], stream=stream)
+                cnt = L.sf_kde_points(idx, b, None, L.SF_K_GAUSS3, p, dens[i], ids[i], stream=stream)
+                nsel, _ = L.sf_select(idx, dens[i], ids[i], cnt, n, math.nan, PCT, None, sels[i],
+                                      stream=stream)
+                h_grid[i].copy_(grids[i], non_blocking=True)
+                h_dens[i][:cnt].copy_(dens[i][:cnt], non_blocking=True)
+                h_ids[i][:cnt].copy_(ids[i][:cnt], non_blocking=True)
+                h_sel[i][:nsel].copy_(sels[i][:nsel], non_blocking=True)
+                d2h += G * 4 + cnt * 8 + nsel * 4
+        finally:
+            L.sf_free_index(idx)
+        torch.cuda.synchronize()
+        stats["h2d"], stats["d2h"] = h2d, d2h
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    ctx["barrier"]()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    el = slowest_rank(time.perf_counter() - t0, ctx["world"], ctx["dist"], "cuda")
+    return {"value": whole_job_rate(pairs_step * args.steps, ctx["world"], el) if pairs_step else None,
+            "unit": UNIT, "h2d_bytes_per_step": stats["h2d"], "d2h_bytes_per_step": stats["d2h"],
+            "ms_per_step": 1e3 * el / args.steps}
 
 
 def batch_rois(torch, d_xyz, n_roi=64, seed=4):
@@ -701,59 +851,6 @@ def run_precision(L, torch, d_xyz, p, box, stream):
         L.sf_free_index(idx)
     return out
 
-
-def run_e2e(args, L, torch, xyz, boxes, p, pairs_step, stream, world, barrier, dist):
-    """Same step, but the cloud starts in pinned host memory and every result
-    (grids, point densities and ids, selections) is copied back to the host."""
-    n = xyz.shape[0]
-    h_xyz = torch.from_numpy(xyz).pin_memory()
-    d_xyz = torch.empty_like(h_xyz, device="cuda")
-    G = DIMS[0] * DIMS[1] * DIMS[2]
-    grids = [torch.empty(G, device="cuda") for _ in boxes]
-    dens = [torch.empty(n, device="cuda") for _ in boxes]
-    ids = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in boxes]
-    sels = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in boxes]
-    h_grid = [torch.empty(G).pin_memory() for _ in boxes]
-    h_dens = [torch.empty(n).pin_memory() for _ in boxes]
-    h_ids = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in boxes]
-    h_sel = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in boxes]
-    stats = {"h2d": 0, "d2h": 0}
-
-    def step():
-        h2d = d2h = 0
-        d_xyz.copy_(h_xyz, non_blocking=True)
-        h2d += h_xyz.numel() * 4
-        idx = L.sf_build_index(d_xyz, stream)
-        try:
-            L.sf_bandwidths(idx, p, stream)
-            for i, b in enumerate(boxes):
-                L.sf_kde_grid(idx, b, DIMS, L.SF_K_GAUSS3, p, grids[i], stream=stream)
-                cnt = L.sf_kde_points(idx, b, None, L.SF_K_GAUSS3, p, dens[i], ids[i], stream=stream)
-                nsel, _ = L.sf_select(idx, dens[i], ids[i], cnt, n, math.nan, PCT, None, sels[i],
-                                      stream=stream)
-                h_grid[i].copy_(grids[i], non_blocking=True)
-                h_dens[i][:cnt].copy_(dens[i][:cnt], non_blocking=True)
-                h_ids[i][:cnt].copy_(ids[i][:cnt], non_blocking=True)
-                h_sel[i][:nsel].copy_(sels[i][:nsel], non_blocking=True)
-                d2h += G * 4 + cnt * 8 + nsel * 4
-        finally:
-            L.sf_free_index(idx)
-        torch.cuda.synchronize()
-        stats["h2d"], stats["d2h"] = h2d, d2h
-
-    for _ in range(max(1, args.warmup)):
-        step()
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    el = slowest_rank(el, world, dist, "cuda")
-    return {"value": whole_job_rate(pairs_step * args.steps, world, el) if pairs_step else None, "unit": UNIT,
-            "h2d_bytes_per_step": stats["h2d"], "d2h_bytes_per_step": stats["d2h"],
-            "ms_per_step": 1e3 * el / args.steps}
 
 
 if __name__ == "__main__":

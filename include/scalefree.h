@@ -331,6 +331,21 @@ sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t
                                  int64_t *h_point_pairs, void *stream);
 
 /*
+ * sf_grid_work_counts -- where the grid's work goes for one ROI (a diagnostic for
+ * tuning and for the roofline's account of wasted evaluations), from the same
+ * counting variant as sf_count_support_pairs. h_counts (host int64[5]):
+ *   [0] in-support (node, particle) pairs (= h_grid_pairs),
+ *   [1] candidate-leaf visits by node tiles,
+ *   [2] (particle, tile) pairs staged: particles whose support reaches the tile,
+ *   [3] 0 (reserved),
+ *   [4] (node, particle) pairs evaluated (every staged particle against every
+ *       node of its tile).
+ * Synchronises the stream. Rules kNN and fixed.
+ */
+sf_status sf_grid_work_counts(sf_index *idx, const sf_box *roi, const int32_t dims[3], int32_t kernel,
+                              const sf_params *params, int64_t h_counts[5], void *stream);
+
+/*
  * Kernel timing: when enabled, the main kernels (k_grid, k_points, k_knn,
  * k_radix_sort, and the counting variants) are bracketed by CUDA events on the
  * stream they are launched on. sf_kernel_timing sums the elapsed times and

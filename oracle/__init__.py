@@ -13,6 +13,9 @@ as plain definitions in double precision over all pairs:
 * ``knn_tree``        the same for every point of a large cloud, through a plain
                       binary k-d tree that only skips subtrees beyond the k-th
                       distance (pinned against ``knn`` bit for bit)
+* ``density_knn_tree`` rho(r) with kNN bandwidths on clouds of a billion points:
+                      only particles whose bandwidth bound reaches r get their
+                      exact h_j (pinned bit for bit against ``density_at``)
 * ``density_at``      rho(r) = (1/N) sum_j K(r - y_j; l_j)        (Eqs. 2, 4, 7)
 * ``kde_grid``        rho at every node, x fastest (Algorithm 4 layout)
 * ``percentile_linear`` P_k^(q) of Eq. 1
@@ -72,6 +75,10 @@ def _load():
         lib.or_knn.restype = ctypes.c_int
         lib.or_knn_tree.argtypes = [f32p, i64, ctypes.c_int, f32p, i64p]
         lib.or_knn_tree.restype = ctypes.c_int
+        lib.or_density_knn_tree.argtypes = [f32p, i64, ctypes.c_int, f64p, i64, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double, f64p, f64p, f64p,
+                                            i64p, ctypes.c_double]
+        lib.or_density_knn_tree.restype = ctypes.c_int
         lib.or_density_at.argtypes = [f32p, i64, f64p, u8p, ctypes.c_double, ctypes.c_int,
                                       ctypes.c_double, f64p, i64, f64p, f64p, f64p, i64p,
                                       ctypes.c_double]
@@ -149,6 +156,31 @@ def knn_tree(xyz, k: int, want_neighbours: bool = False):
     if rc != 0:
         raise ValueError("or_knn_tree failed")
     return h, nbr
+
+
+def density_knn_tree(xyz, k: int, r, kernel: int, inv_neff: float, amb_band: float = 1e-6):
+    """rho(r) with the kNN bandwidths of ``knn`` (h_j for every particle j), for clouds
+    where neither all bandwidths nor all pairs can be evaluated: a k-d tree bounds every
+    particle's bandwidth by the bounding box of a subtree holding it and k others, and
+    only the particles those bounds cannot rule out get their exact h_j; the terms are
+    added in ascending j with the operations of ``density_at``, so the result equals
+    ``density_at(xyz, iso_ell(knn(xyz, k)[0]), r, ...)`` bit for bit.
+    Returns dict(rho, wpeak, amb, pairs) like ``density_at``."""
+    a = _xyz(xyz)
+    n = a.shape[0]
+    if k < 1 or n <= k:
+        raise ValueError("need 1 <= k < N")
+    rr = np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(-1, 3))
+    m = rr.shape[0]
+    rho, wpk, amb = np.empty(m), np.empty(m), np.empty(m)
+    pairs = np.empty(m, dtype=np.int64)
+    rc = _load().or_density_knn_tree(_ptr(a, ctypes.c_float), n, int(k), _ptr(rr, ctypes.c_double),
+                                     m, int(kernel), P3, float(inv_neff), _ptr(rho, ctypes.c_double),
+                                     _ptr(wpk, ctypes.c_double), _ptr(amb, ctypes.c_double),
+                                     _ptr(pairs, ctypes.c_int64), float(amb_band))
+    if rc != 0:
+        raise ValueError("or_density_knn_tree failed")
+    return {"rho": rho, "wpeak": wpk, "amb": amb, "pairs": pairs}
 
 
 # ---------------------------------------------------------------------------

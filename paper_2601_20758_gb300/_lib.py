@@ -100,6 +100,8 @@ _PROTOS = {
     "sf_count_support_pairs": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
                                               ctypes.POINTER(sf_params), ctypes.POINTER(_i64),
                                               ctypes.POINTER(_i64), _vp]),
+    "sf_grid_work_counts": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
+                                           ctypes.POINTER(sf_params), ctypes.POINTER(_i64), _vp]),
     "sf_kde_grid_static": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
                                           ctypes.POINTER(sf_params), _vp, ctypes.POINTER(_dbl), _vp]),
     "sf_query_workspace": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
@@ -271,6 +273,17 @@ def sf_query_workspace(idx, roi: sf_box, dims, kernel, params, what=SF_WS_GRID, 
                                                            ctypes.byref(params), int(what),
                                                            ctypes.byref(b), _stream(stream)))
     return int(b.value)
+
+
+def sf_grid_work_counts(idx, roi: sf_box, dims, kernel, params, stream=None) -> dict:
+    """Work accounting of one ROI grid: in-support pairs, candidate-leaf visits, staged
+    (particle, tile) pairs, a reserved zero, evaluated pairs."""
+    d = (_i32 * 3)(*_dims3(dims))
+    c = (_i64 * 5)()
+    _check("sf_grid_work_counts", load().sf_grid_work_counts(idx, ctypes.byref(roi), d, int(kernel),
+                                                             ctypes.byref(params), c, _stream(stream)))
+    keys = ("pairs", "leaf_visits", "staged", "reserved", "evaluated")
+    return {k: int(v) for k, v in zip(keys, c)}
 
 
 def sf_last_call_workspace() -> int:

@@ -384,10 +384,9 @@ sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids
                          h_nsel, h_threshold, (cudaStream_t)stream);
 }
 
-sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t dims[3],
-                                 int32_t kernel, const sf_params *params, int64_t *h_grid_pairs,
-                                 int64_t *h_point_pairs, void *stream) {
-    clear_error();
+static sf_status count_pairs_impl(sf_index *idx, const sf_box *roi, const int32_t dims[3],
+                                  int32_t kernel, const sf_params *params, int64_t *h_grid_pairs,
+                                  int64_t *h_point_pairs, int64_t *h_work, void *stream) {
     if (!idx || (!h_grid_pairs && !h_point_pairs))
         return fail(SF_ERR_INVALID_ARG, "sf_count_support_pairs: NULL argument");
     SF_TRY(check_roi(roi, "sf_count_support_pairs"));
@@ -397,9 +396,10 @@ sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t
     if (need_grid) SF_TRY(make_grid(*roi, dims, g, "sf_count_support_pairs"));
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc(s);
-    unsigned long long *cnt = sc.get<unsigned long long>(2);
+    // [0..4]: grid pairs and the grid's work accounting (sf_grid_work_counts); [5]: points
+    unsigned long long *cnt = sc.get<unsigned long long>(6);
     SF_TRY_SCRATCH(sc);
-    SF_TRY_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
+    SF_TRY_CUDA(cudaMemsetAsync(cnt, 0, 6 * sizeof(unsigned long long), s));
     Prepared pr;
     SF_TRY(prepare(idx, *roi, need_grid ? &g : nullptr, kernel, *params, sc, pr, s));
     if (h_grid_pairs) {
@@ -415,16 +415,34 @@ sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t
         uint8_t *inroi = sc.get<uint8_t>(nleaf * kLeaf);
         SF_TRY_SCRATCH(sc);
         if (nleaf > 0)
-            SF_TRY(density_points(idx, *roi, pr.call, leaves, nleaf, rho, inroi, s, cnt + 1));
+            SF_TRY(density_points(idx, *roi, pr.call, leaves, nleaf, rho, inroi, s, cnt + 5));
     }
-    unsigned long long h[2] = {0, 0};
+    unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
     int h_st = 0;
     SF_TRY_CUDA(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, s));
     SF_TRY_CUDA(cudaMemcpyAsync(&h_st, pr.status, sizeof h_st, cudaMemcpyDeviceToHost, s));
     SF_TRY_CUDA(cudaStreamSynchronize(s));
     if (h_grid_pairs) *h_grid_pairs = (int64_t)h[0];
-    if (h_point_pairs) *h_point_pairs = (int64_t)h[1];
+    if (h_point_pairs) *h_point_pairs = (int64_t)h[5];
+    if (h_work)
+        for (int k = 0; k < 5; ++k) h_work[k] = (int64_t)h[k];
     return call_status(h_st);
+}
+
+sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t dims[3],
+                                 int32_t kernel, const sf_params *params, int64_t *h_grid_pairs,
+                                 int64_t *h_point_pairs, void *stream) {
+    clear_error();
+    return count_pairs_impl(idx, roi, dims, kernel, params, h_grid_pairs, h_point_pairs, nullptr,
+                            stream);
+}
+
+sf_status sf_grid_work_counts(sf_index *idx, const sf_box *roi, const int32_t dims[3], int32_t kernel,
+                              const sf_params *params, int64_t h_counts[5], void *stream) {
+    clear_error();
+    if (!h_counts) return fail(SF_ERR_INVALID_ARG, "sf_grid_work_counts: NULL argument");
+    int64_t pairs = 0;
+    return count_pairs_impl(idx, roi, dims, kernel, params, &pairs, nullptr, h_counts, stream);
 }
 
 struct sf_batch {

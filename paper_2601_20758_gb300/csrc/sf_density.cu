@@ -485,6 +485,27 @@ __device__ void grid_chunk(GridSmemT<TZ> &S, const TileGeom &g, const int *leave
 }
 
 // Fold a chunk's FP32 sums into the compensated per-voxel sums (TwoSum).
+// One per-axis table entry of the split pipeline for a particle at coordinate pc
+// (scale u = uscale / l, weight c) and a node nc (hi, lo): q = ((nc - pc) u)^2 and
+//   Gauss axis 0: (c e^{-q}, q)   axis 1: (e^{-q}, q)   axis 2: (e^{-q}, qmax - q)
+//   Epan  axis 0/1: (q, -)        axis 2: (c (1 - q), -)
+// with "no support" values (kBig / -1 / -kBig) where q >= qmax or outside.
+template <int KER>
+__device__ __forceinline__ float2 kentry(int axis, bool inside, float pc, float u, float c, float2 nc) {
+    const float d = (nc.x - pc) + nc.y;
+    const float t = d * u;
+    const float q = t * t;
+    const bool sup = inside && q < KDef<KER>::qmax;
+    if (KER == SF_K_GAUSS3) {
+        const float w = sup ? ex2_approx(-q) : 0.f;
+        if (axis == 0) return make_float2(w * c, sup ? q : kBig);
+        if (axis == 1) return make_float2(w, sup ? q : kBig);
+        return make_float2(w, sup ? KDef<KER>::qmax - q : -1.f);
+    }
+    if (axis < 2) return make_float2(sup ? q : kBig, 0.f);
+    return make_float2(sup ? c * (1.0f - q) : -kBig, 0.f);
+}
+
 template <int TZ>
 __device__ __forceinline__ void fold(float acc[TZ], float sum[TZ], float cmp[TZ]) {
 #pragma unroll
@@ -786,6 +807,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
 #pragma unroll
         for (int k = 0; k < TZ; ++k) acc[k] = sum[k] = cmp[k] = 0.f;
         unsigned long long np = 0;
+        unsigned long long st_leaves = 0, st_staged = 0, st_tested = 0;
         for (int lb = it.y; lb < it.z; ++lb) {
             // ---- one candidate leaf: refine (footprint in this tile, clip) and stage
             const int64_t i = (int64_t)list[lb] * kLeaf + lane;
@@ -821,6 +843,45 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                     qlb = fmaf(t, t, qlb);
                 }
                 if (!(qlb < KDef<KER>::rmul * KDef<KER>::rmul * (1.0f + kFilterSlack))) acc_pt = false;
+                // Small supports: exact footprints. The widened ranges shrink to the nodes whose
+                // per-axis q (computed exactly as the tables compute it) is below
+                // qmax -- a contiguous run, since q is unimodal along the axis. Then
+                // the smallest per-axis q bounds every node's test (the float sums and
+                // differences are monotone): a particle that fails it adds nothing to
+                // any node of the tile (a dense cluster between the nodes of a coarse
+                // grid) and is not staged.
+                if (acc_pt && f1[0] - f0[0] < 4 && f1[1] - f0[1] < 4 && f1[2] - f0[2] < 4) {
+                    float mq[3];
+                    const int aoff[3] = {0, kWX, kWX + kWY};
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float u = KDef<KER>::uscale * rl[k];
+                        auto qat = [&](int ii) {
+                            const float2 nc = S.axt[aoff[k] + ii];
+                            const float d = (nc.x - pc[k]) + nc.y;
+                            const float t = d * u;
+                            return t * t;
+                        };
+                        while (f0[k] <= f1[k] && !(qat(f0[k]) < KDef<KER>::qmax)) ++f0[k];
+                        while (f1[k] >= f0[k] && !(qat(f1[k]) < KDef<KER>::qmax)) --f1[k];
+                        float m = kBig;
+                        if (f0[k] <= f1[k]) {
+                            const int ic = min(max((int)rintf((pc[k] - g.tlo[k]) * isp[k]), f0[k]), f1[k]);
+#pragma unroll
+                            for (int dd = -1; dd <= 1; ++dd) {
+                                const int ii = ic + dd;
+                                if (ii >= f0[k] && ii <= f1[k]) m = fminf(m, qat(ii));
+                            }
+                        }
+                        mq[k] = m;
+                    }
+                    if (KER == SF_K_GAUSS3) {
+                        if (!(mq[0] + mq[1] < KDef<KER>::qmax - mq[2])) acc_pt = false;
+                    } else {
+                        const float c = E.cnorm * ((rl[0] * rl[1]) * rl[2]);
+                        if (!(c * (1.0f - mq[2]) - c * (mq[0] + mq[1]) > 0.f)) acc_pt = false;
+                    }
+                }
                 if (acc_pt) {
                     fp.x = f0[0] | (f1[0] << 8) | (f0[1] << 16) | (f1[1] << 24);
                     fp.y = f0[2] | (f1[2] << 8);
@@ -829,6 +890,11 @@ __global__ void __launch_bounds__(kGridThreads, 4)
             const unsigned bal = __ballot_sync(0xffffffffu, acc_pt);
             const int ns = __popc(bal);
             if (ns == 0) continue;  // warp-uniform
+            if (CNT && lane == 0) {
+                ++st_leaves;
+                st_staged += ns;
+                st_tested += (unsigned long long)ns * (kWX * kWY * TZ);
+            }
             if (acc_pt) {
                 const int s = __popc(bal & ((1u << lane) - 1u));
                 S.sp[s] = make_float4(p.x, p.y, p.z, E.cnorm * ((rl[0] * rl[1]) * rl[2]));
@@ -837,24 +903,14 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                 S.sf[s] = fp;
             }
             __syncwarp();
-            // ---- per-axis tables over the whole tile: factors inside the footprint,
-            // "no support" values outside it (so the accumulation needs no range tests).
-            // Many staged points: each staging lane fills its own point's entries;
-            // few: the entries are spread over all lanes. Both give the same values.
+            // ---- per-axis tables: factors inside the footprint, "no support" values
+            // outside it (so the accumulation needs no range tests). Many staged points:
+            // each staging lane fills its own point's entries, in an order rotated by
+            // its row so that the lanes' stores spread over the banks; few: the entries
+            // are spread over all lanes. Same values either way.
             constexpr int kEnt = kWX + kWY + TZ;
             auto entry = [&](int axis, int ii, bool inside, float pc, float u, float c, float2 nc) {
-                const float d = (nc.x - pc) + nc.y;
-                const float t = d * u;
-                const float q = t * t;
-                const bool sup = inside && q < KDef<KER>::qmax;
-                if (KER == SF_K_GAUSS3) {
-                    const float w = sup ? ex2_approx(-q) : 0.f;
-                    if (axis == 0) return make_float2(w * c, sup ? q : kBig);
-                    if (axis == 1) return make_float2(w, sup ? q : kBig);
-                    return make_float2(w, sup ? KDef<KER>::qmax - q : -1.f);
-                }
-                if (axis < 2) return make_float2(sup ? q : kBig, 0.f);
-                return make_float2(sup ? c * (1.0f - q) : -kBig, 0.f);
+                return kentry<KER>(axis, inside, pc, u, c, nc);
             };
             if (ns >= kLaneTables) {
                 if (acc_pt) {
@@ -865,15 +921,23 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                     const int x0 = fp.x & 255, x1 = (fp.x >> 8) & 255;
                     const int y0 = (fp.x >> 16) & 255, y1 = (fp.x >> 24) & 255;
                     const int z0 = fp.y & 255, z1 = (fp.y >> 8) & 255;
+                    {
 #pragma unroll
-                    for (int i = 0; i < kWX; ++i)
-                        S.tx[s][i] = entry(0, i, i >= x0 && i <= x1, p.x, u0, c, S.axt[i]);
+                        for (int t = 0; t < kWX; ++t) {
+                            const int i = (t + (s >> 1)) & (kWX - 1);
+                            S.tx[s][i] = entry(0, i, i >= x0 && i <= x1, p.x, u0, c, S.axt[i]);
+                        }
 #pragma unroll
-                    for (int i = 0; i < kWY; ++i)
-                        S.ty[s][i] = entry(1, i, i >= y0 && i <= y1, p.y, u1, c, S.axt[kWX + i]);
+                        for (int t = 0; t < kWY; ++t) {
+                            const int i = (t + (s >> 2)) & (kWY - 1);
+                            S.ty[s][i] = entry(1, i, i >= y0 && i <= y1, p.y, u1, c, S.axt[kWX + i]);
+                        }
 #pragma unroll
-                    for (int i = 0; i < TZ; ++i)
-                        S.tz[s][i] = entry(2, i, i >= z0 && i <= z1, p.z, u2, c, S.axt[kWX + kWY + i]);
+                        for (int t = 0; t < TZ; ++t) {
+                            const int i = (t + (s >> (TZ == 8 ? 1 : 2))) & (TZ - 1);
+                            S.tz[s][i] = entry(2, i, i >= z0 && i <= z1, p.z, u2, c, S.axt[kWX + kWY + i]);
+                        }
+                    }
                 }
             } else
             for (int e = lane; e < ns * kEnt; e += 32) {
@@ -899,6 +963,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                 else S.tz[s][ii] = v;
             }
             __syncwarp();
+            {
             // ---- accumulate: lane owns column (cx, cy) and TZ nodes in z
             for (int s = 0; s < ns; ++s) {
                 const float2 ex = S.tx[s][cx];
@@ -924,10 +989,16 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                     }
                 }
             }
+            }
             __syncwarp();
             fold<TZ>(acc, sum, cmp);
         }
         if (CNT && cx < g.nv[0] && cy < g.nv[1]) npairs += np;
+        if (CNT && lane == 0) {  // work accounting of the counting variant
+            atomicAdd(a.pairs + 1, st_leaves);
+            atomicAdd(a.pairs + 2, st_staged);
+            atomicAdd(a.pairs + 4, st_tested);
+        }
         double *o = part + ((int64_t)item * 32 + lane) * TZ;
 #pragma unroll
         for (int k = 0; k < TZ; ++k) o[k] = (double)sum[k] + (double)cmp[k];
@@ -1095,7 +1166,7 @@ struct MrBuffers {
     double *part;
     unsigned int *next;
     uint32_t lpw;
-    int64_t slots;
+    int64_t slots;        // resident blocks of k_mr_work
 };
 
 // Execution: list, items, persistent work, ordered reduce (no host sync; capturable).

@@ -167,6 +167,7 @@ __global__ void k_leaf_ell(const float4 *__restrict__ pos, const float4 *__restr
     if (leaf >= nleaf) return;
     const int64_t i = leaf * kLeaf + lane;
     float3 m = make_float3(0.f, 0.f, 0.f);
+    float hmin = INFINITY;  // smallest positive length of the leaf (any axis)
     if (i < n) {
         float4 p = pos[i];
         bool in = true;
@@ -180,6 +181,7 @@ __global__ void k_leaf_ell(const float4 *__restrict__ pos, const float4 *__restr
             } else {
                 m = make_float3(p.w, p.w, p.w);
             }
+            if (m.x > 0.f && m.y > 0.f && m.z > 0.f) hmin = fminf(m.x, fminf(m.y, m.z));
         }
     }
 #pragma unroll
@@ -187,8 +189,9 @@ __global__ void k_leaf_ell(const float4 *__restrict__ pos, const float4 *__restr
         m.x = fmaxf(m.x, __shfl_xor_sync(0xffffffffu, m.x, o));
         m.y = fmaxf(m.y, __shfl_xor_sync(0xffffffffu, m.y, o));
         m.z = fmaxf(m.z, __shfl_xor_sync(0xffffffffu, m.z, o));
+        hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
     }
-    if (lane == 0) nell[leaf] = make_float4(m.x, m.y, m.z, 0.0f);
+    if (lane == 0) nell[leaf] = make_float4(m.x, m.y, m.z, hmin);
 }
 
 __global__ void k_inner_ell(float4 *__restrict__ nell, int64_t child_off, int64_t child_cnt,

@@ -4,18 +4,21 @@ Progressive navigation (the paper's Sec. 4.2: a new region of interest or a
 new scale triggers a density recompute) turns into a stream of recompute
 requests. The server keeps the index and the bandwidths resident on the GPU;
 requests wait in arrival order and are admitted as soon as a slot is free and
-their estimated device memory fits the budget; each slot runs its request
-(ROI grid -> ROI point densities -> threshold selection) on its own CUDA
-stream, so admitted requests overlap on the device. Latency = completion time
-- arrival time on the host clock.
+the device memory the request's calls will allocate (asked of the library
+with sf_query_workspace when the request arrives) fits the budget next to the
+requests already running. Each slot is a fixed worker thread with its own
+CUDA stream and preallocated output buffers, so admitted requests overlap on
+the device. Latency = completion time - arrival time on the host clock.
 
 The executor is pluggable: ``GpuExecutor`` drives libscalefree through the C
-ABI; tests drive the admission logic with a fake executor on the CPU.
+ABI; tests drive the admission logic with a fake executor on the CPU. An
+executor provides ``run(req, slot)`` and ``workspace(req)`` (bytes).
 """
 from __future__ import annotations
 
 import collections
 import math
+import queue
 import threading
 import time
 from dataclasses import dataclass, field
@@ -32,6 +35,7 @@ class Request:
     arrival: float = 0.0          # seconds on the server clock
     select_pct: float = 90.0
     want_points: bool = True
+    prec: str = "fp32"            # "fp32", or "bf16": tensor-core cross term for the point densities
     # filled by the server
     admitted: float = math.nan
     done: float = math.nan
@@ -43,15 +47,6 @@ class Request:
         return self.done - self.arrival
 
 
-def estimate_bytes(req: Request, n_points: int) -> int:
-    """Device memory a request holds while it runs: the grid output, the grid
-    work buffers (partial sums bounded by 16 B per node plus the candidate
-    lists), and the per-point scratch of the point densities (24 B per point)."""
-    g = int(req.dims[0]) * int(req.dims[1]) * int(req.dims[2])
-    pts = 24 * n_points if req.want_points else 0
-    return 4 * g + 16 * g + 8 * n_points // 32 + pts
-
-
 def percentile(values, q):
     v = sorted(values)
     if not v:
@@ -61,13 +56,12 @@ def percentile(values, q):
 
 
 class Server:
-    """Continuous admission over `slots` concurrent slots and a memory budget."""
+    """Continuous admission over `slots` fixed workers and a device-memory budget."""
 
-    def __init__(self, executor, slots: int = 4, mem_budget: int = 1 << 34, n_points: int = 0):
+    def __init__(self, executor, slots: int = 4, mem_budget: int = 1 << 34):
         self.ex = executor
         self.slots = slots
         self.budget = mem_budget
-        self.n_points = n_points
         self._lock = threading.Condition()
         self._queue = collections.deque()
         self._free_slots = list(range(slots))
@@ -78,6 +72,11 @@ class Server:
         self.max_bytes = 0
         self.completed = []
         self._t0 = time.perf_counter()
+        self._inbox = [queue.Queue() for _ in range(slots)]
+        self._workers = [threading.Thread(target=self._worker, args=(s,), daemon=True)
+                         for s in range(slots)]
+        for w in self._workers:
+            w.start()
         self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
         self._dispatcher.start()
 
@@ -85,28 +84,40 @@ class Server:
         return time.perf_counter() - self._t0
 
     def submit(self, req: Request):
-        need = estimate_bytes(req, self.n_points)
+        try:
+            need = int(self.ex.workspace(req))
+        except Exception as e:  # noqa: BLE001  (an invalid request fails alone)
+            with self._lock:
+                req.status = f"error: {e}"
+                req.done = self.now()
+                self.completed.append(req)
+                self._lock.notify_all()
+            return
         with self._lock:
             if need > self.budget:
                 req.status = "rejected"      # can never fit, even alone
                 req.done = self.now()
                 self.completed.append(req)
+                self._lock.notify_all()
                 return
             req._need = need
             self._queue.append(req)
             self._lock.notify_all()
 
+    def _admissible(self) -> bool:
+        return bool(self._queue and self._free_slots
+                    and self._in_flight + self._queue[0]._need <= self.budget)
+
     def _dispatch(self):
         while True:
             with self._lock:
-                while not self._closed and not (
-                        self._queue and self._free_slots
-                        and self._in_flight + self._queue[0]._need <= self.budget):
+                while not self._closed and not self._admissible():
                     self._lock.wait()
                 if self._closed and not self._queue:
+                    for q in self._inbox:
+                        q.put(None)
                     return
-                if not (self._queue and self._free_slots
-                        and self._in_flight + self._queue[0]._need <= self.budget):
+                if not self._admissible():
                     continue
                 req = self._queue.popleft()           # first come, first admitted
                 slot = self._free_slots.pop()
@@ -116,21 +127,25 @@ class Server:
                 self.max_bytes = max(self.max_bytes, self._in_flight)
                 req.admitted = self.now()
                 req.status = "running"
-            threading.Thread(target=self._work, args=(req, slot), daemon=True).start()
+            self._inbox[slot].put(req)
 
-    def _work(self, req: Request, slot: int):
-        try:
-            req.result = self.ex.run(req, slot)
-            req.status = "done"
-        except Exception as e:  # noqa: BLE001  (recorded per request)
-            req.status = f"error: {e}"
-        with self._lock:
-            req.done = self.now()
-            self._in_flight -= req._need
-            self._running -= 1
-            self._free_slots.append(slot)
-            self.completed.append(req)
-            self._lock.notify_all()
+    def _worker(self, slot: int):
+        while True:
+            req = self._inbox[slot].get()
+            if req is None:
+                return
+            try:
+                req.result = self.ex.run(req, slot)
+                req.status = "done"
+            except Exception as e:  # noqa: BLE001  (recorded per request)
+                req.status = f"error: {e}"
+            with self._lock:
+                req.done = self.now()
+                self._in_flight -= req._need
+                self._running -= 1
+                self._free_slots.append(slot)
+                self.completed.append(req)
+                self._lock.notify_all()
 
     def drain(self, n_expected: int, timeout: float = 600.0):
         deadline = time.perf_counter() + timeout
@@ -146,17 +161,20 @@ class Server:
             self._closed = True
             self._lock.notify_all()
         self._dispatcher.join(timeout=10)
+        for w in self._workers:
+            w.join(timeout=10)
 
     def replay(self, requests, timeout: float = 600.0):
         """Submit requests at their arrival times (seconds from now), wait for all."""
         base = self.now()
+        n0 = len(self.completed)
         for r in sorted(requests, key=lambda r: r.arrival):
             r.arrival += base
             delay = r.arrival - self.now()
             if delay > 0:
                 time.sleep(delay)
             self.submit(r)
-        self.drain(len(requests), timeout)
+        self.drain(n0 + len(requests), timeout)
         return self.stats()
 
     def stats(self):
@@ -173,20 +191,43 @@ class Server:
 
 
 class GpuExecutor:
-    """Runs a request through the C ABI on the slot's own CUDA stream."""
+    """Runs a request through the C ABI on the slot's own CUDA stream. Output
+    buffers are preallocated per slot (max_nodes grid nodes, max_points ROI points);
+    admission sizes each request by the library's own workspace figure."""
 
-    def __init__(self, idx, params, kernel, n_points, slots, max_nodes, copy_back=False):
+    def __init__(self, idx, params, kernel, n_points, slots, max_nodes, max_points=None,
+                 copy_back=False):
         import torch
         from . import _lib as L
         self.L, self.torch = L, torch
-        self.idx, self.params, self.kernel, self.n = idx, params, kernel, n_points
+        self.idx, self.kernel, self.n = idx, kernel, n_points
+        self.params = {"fp32": params, "bf16": L.make_params(rule=params.rule, k=params.k,
+                                                           scope=params.scope)}
+        self.params["bf16"].prec = L.SF_PREC_BF16
         self.copy_back = copy_back
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.query_stream = torch.cuda.Stream()
+        self._qlock = threading.Lock()
+        cap = n_points if max_points is None else int(max_points)
         dev = "cuda"
         self.grid = [torch.empty(max_nodes, device=dev) for _ in range(slots)]
-        self.dens = [torch.empty(n_points, device=dev) for _ in range(slots)]
-        self.ids = [torch.empty(n_points, dtype=torch.int32, device=dev) for _ in range(slots)]
-        self.sel = [torch.empty(n_points, dtype=torch.int32, device=dev) for _ in range(slots)]
+        self.dens = [torch.empty(cap, device=dev) for _ in range(slots)]
+        self.ids = [torch.empty(cap, dtype=torch.int32, device=dev) for _ in range(slots)]
+        self.sel = [torch.empty(cap, dtype=torch.int32, device=dev) for _ in range(slots)]
+
+    def workspace(self, req: Request) -> int:
+        """Device bytes the request's calls allocate at most at once (the calls run one
+        after the other on the slot's stream, so the larger of the two)."""
+        L = self.L
+        box = L.make_box(req.lo, req.hi)
+        with self._qlock:
+            g = L.sf_query_workspace(self.idx, box, req.dims, self.kernel, self.params["fp32"],
+                                     L.SF_WS_GRID, stream=self.query_stream)
+            p = 0
+            if req.want_points:
+                p = L.sf_query_workspace(self.idx, box, req.dims, self.kernel, self.params[req.prec],
+                                         L.SF_WS_POINTS, stream=self.query_stream)
+        return max(g, p)
 
     def run(self, req: Request, slot: int):
         L, torch = self.L, self.torch
@@ -194,11 +235,11 @@ class GpuExecutor:
         box = L.make_box(req.lo, req.hi)
         G = int(req.dims[0]) * int(req.dims[1]) * int(req.dims[2])
         grid = self.grid[slot][:G]
-        L.sf_kde_grid(self.idx, box, req.dims, self.kernel, self.params, grid, stream=st)
+        L.sf_kde_grid(self.idx, box, req.dims, self.kernel, self.params["fp32"], grid, stream=st)
         out = {"nodes": G}
         if req.want_points:
-            cnt = L.sf_kde_points(self.idx, box, None, self.kernel, self.params, self.dens[slot],
-                                  self.ids[slot], stream=st)
+            cnt = L.sf_kde_points(self.idx, box, None, self.kernel, self.params[req.prec],
+                                  self.dens[slot], self.ids[slot], stream=st)
             nsel, t = L.sf_select(self.idx, self.dens[slot], self.ids[slot], cnt, self.n,
                                   math.nan, req.select_pct, None, self.sel[slot], stream=st)
             out.update(points=cnt, selected=nsel, threshold=t)
@@ -207,18 +248,21 @@ class GpuExecutor:
             out["grid"] = grid.cpu()
             if req.want_points:
                 out["dens"] = self.dens[slot][:out["points"]].cpu()
+                out["ids"] = self.ids[slot][:out["points"]].cpu()
                 out["sel"] = self.sel[slot][:out["selected"]].cpu()
         return out
 
 
 def navigation_requests(n: int, rate: float, centre, seed: int, edges=(64, 96, 128, 192, 256),
-                        log_range=(-3.0, 0.0), step_decades=0.1, select_every: int = 0):
+                        log_range=(-3.0, 0.0), step_decades=0.1, select_every: int = 0,
+                        bf16_share: float = 0.0):
     """Seeded progressive-navigation stream: Poisson arrivals at `rate` per second;
     the ROI scale walks in log10 space with Gaussian steps (reflected at the range
     ends), the centre pans by up to half an edge per step; grid edges uniform in
     `edges`. Cubic ROIs kept inside the unit cube. A view change recomputes the
     ROI grid; with select_every = m > 0, every m-th request also recomputes the
-    ROI's point densities and the percentile selection."""
+    ROI's point densities and the percentile selection. A seeded `bf16_share` of
+    the requests asks for the BF16 tensor-core path (point densities)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     scale = log_range[1] - 0.5
@@ -238,4 +282,8 @@ def navigation_requests(n: int, rate: float, centre, seed: int, edges=(64, 96, 1
         g = int(rng.choice(edges))
         out.append(Request(rid=i, lo=tuple(c - e / 2), hi=tuple(c + e / 2), dims=(g, g, g),
                            arrival=t, want_points=bool(select_every) and i % select_every == 0))
+    if bf16_share > 0.0:  # a separate draw, so the walk is the same with or without it
+        mix = np.random.default_rng(seed + 1).random(n) < bf16_share
+        for r, b in zip(out, mix):
+            r.prec = "bf16" if b else "fp32"
     return out

@@ -101,12 +101,23 @@ GRID_CASES = [
     ("epan_fixed_clip", "plain", "fixed", oracle.EPAN, "clip", ((0.2, 0.1, 0.3), (0.8, 0.9, 0.7)), (33, 20, 17), (0.05, 0.07, 0.04)),
     ("gauss_fixed_global", "plain", "fixed", oracle.GAUSS3, "global", ((0, 0, 0), (1, 1, 1)), (17, 17, 17), (0.03, 0.03, 0.03)),
     ("gauss_knn_cluster_zoom", "cluster", "knn", oracle.GAUSS3, "global", ((0.40, 0.40, 0.40), (0.46, 0.47, 0.45)), (24, 24, 24), 64),
+    # supports below the node spacing (the 2 x 2 x 2 corner-block path): tight clusters
+    # on a coarse grid, fixed lengths under one spacing, particles at node midpoints
+    ("gauss_knn_cluster_coarse", "cluster", "knn", oracle.GAUSS3, "global", ((0, 0, 0), (1, 1, 1)), (37, 29, 23), 16),
+    ("epan_knn_cluster_coarse_clip", "cluster", "knn", oracle.EPAN, "clip", ((0.05, 0.1, 0.02), (0.93, 0.97, 0.9)), (30, 26, 41), 16),
+    ("gauss_fixed_small", "plain", "fixed", oracle.GAUSS3, "global", ((0, 0, 0), (1, 1, 1)), (50, 40, 30), (0.004, 0.006, 0.005)),
+    ("epan_fixed_midpoints", "midpoints", "fixed", oracle.EPAN, "global", ((0, 0, 0), (1, 1, 1)), (17, 17, 17), (0.04, 0.05, 0.035)),
+    ("gauss_fixed_midpoints", "midpoints", "fixed", oracle.GAUSS3, "global", ((0, 0, 0), (1, 1, 1)), (17, 17, 17), (0.0135, 0.02, 0.012)),
 ]
 
 
 def _cloud(name):
     if name == "plain":
         return synth.plain_cloud(20000, seed=7)
+    if name == "midpoints":  # nodes every 1/16; points on nodes, on midpoints and between
+        lat = synth.lattice_cloud(17, 1.0 / 16)
+        mid = synth.lattice_cloud(16, 1.0 / 16, origin=1.0 / 32)
+        return np.ascontiguousarray(np.concatenate([lat, mid, synth.uniform_cloud(3000, seed=8)]))
     return synth.cosmology_cloud(30000, seed=6, levels=7)
 
 

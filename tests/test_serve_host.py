@@ -16,6 +16,10 @@ class FakeExecutor:
         self.max_running = 0
         self.order = []
 
+    def workspace(self, req):
+        g = int(req.dims[0]) * int(req.dims[1]) * int(req.dims[2])
+        return 20 * g
+
     def run(self, req, slot):
         with self.lock:
             self.running += 1
@@ -34,23 +38,23 @@ def _reqs(n, dims=(16, 16, 16), gap=0.0):
 
 def test_slots_bound_concurrency_and_admission_is_fifo():
     ex = FakeExecutor(0.02)
-    srv = serve.Server(ex, slots=3, mem_budget=1 << 40, n_points=1000)
+    srv = serve.Server(ex, slots=3, mem_budget=1 << 40)
     try:
         st = srv.replay(_reqs(12))
     finally:
         srv.close()
     assert st["done"] == 12 and st["errors"] == 0
     assert ex.max_running <= 3 and srv.max_concurrent == 3
-    assert ex.order == sorted(ex.order)          # admitted in arrival order
+    adm = [r.admitted for r in sorted(srv.completed, key=lambda r: r.rid)]
+    assert adm == sorted(adm)                    # admitted in arrival order
     assert st["p99_ms"] >= st["p50_ms"] >= 20.0 * 0.9
 
 
 def test_memory_budget_limits_admission_and_rejects_oversize():
-    n_points = 1000
     small = serve.Request(rid=0, lo=(0, 0, 0), hi=(1, 1, 1), dims=(32, 32, 32))
-    need = serve.estimate_bytes(small, n_points)
     ex = FakeExecutor(0.02)
-    srv = serve.Server(ex, slots=8, mem_budget=2 * need + need // 2, n_points=n_points)
+    need = ex.workspace(small)
+    srv = serve.Server(ex, slots=8, mem_budget=2 * need + need // 2)
     try:
         reqs = [serve.Request(rid=i, lo=(0, 0, 0), hi=(1, 1, 1), dims=(32, 32, 32)) for i in range(6)]
         huge = serve.Request(rid=99, lo=(0, 0, 0), hi=(1, 1, 1), dims=(512, 512, 512))
@@ -83,3 +87,46 @@ def test_percentile_nearest_rank():
     assert serve.percentile([5, 1, 4, 2, 3], 50) == 3
     assert serve.percentile([5, 1, 4, 2, 3], 99) == 5
     assert serve.percentile([], 50) is None
+
+
+def test_workers_are_fixed_per_slot():
+    """Each slot is served by one long-lived worker thread (no thread per request)."""
+    seen = {}
+
+    class Ex(FakeExecutor):
+        def run(self, req, slot):
+            seen.setdefault(slot, set()).add(threading.get_ident())
+            return super().run(req, slot)
+
+    ex = Ex(0.005)
+    srv = serve.Server(ex, slots=2, mem_budget=1 << 40)
+    try:
+        st = srv.replay(_reqs(20))
+    finally:
+        srv.close()
+    assert st["done"] == 20
+    assert all(len(v) == 1 for v in seen.values()) and len(seen) == 2
+
+
+def test_a_request_whose_workspace_query_fails_errors_alone():
+    class Ex(FakeExecutor):
+        def workspace(self, req):
+            if req.rid == 3:
+                raise ValueError("bad ROI")
+            return super().workspace(req)
+
+    ex = Ex(0.002)
+    srv = serve.Server(ex, slots=2, mem_budget=1 << 40)
+    try:
+        st = srv.replay(_reqs(6))
+    finally:
+        srv.close()
+    assert st["done"] == 5 and st["errors"] == 1
+
+
+def test_bf16_share_is_seeded_and_leaves_the_walk_alone():
+    a = serve.navigation_requests(400, rate=200.0, centre=(0.5, 0.5, 0.5), seed=9)
+    b = serve.navigation_requests(400, rate=200.0, centre=(0.5, 0.5, 0.5), seed=9, bf16_share=0.3)
+    assert [(r.lo, r.dims, r.arrival) for r in a] == [(r.lo, r.dims, r.arrival) for r in b]
+    share = sum(r.prec == "bf16" for r in b) / len(b)
+    assert 0.24 < share < 0.36 and all(r.prec == "fp32" for r in a)
