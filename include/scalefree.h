@@ -70,11 +70,15 @@ enum { SF_BW_KNN = 0, SF_BW_MBE = 1, SF_BW_FIXED = 2 };
  * SF_SCOPE_GLOBAL: all particles, N_eff = N. */
 enum { SF_SCOPE_CLIP = 0, SF_SCOPE_GLOBAL = 1 };
 
-/* Precision of the point densities (sf_kde_points, DIRECT, kNN bandwidths):
- * FP32 everywhere, or the squared-distance cross term on tensor cores in TF32
- * (one pass), 3xTF32 (hi/lo split, three passes) or BF16 (one pass, 8
- * significant bits); see sf_kde_points. Grids and every other call are FP32
- * only. */
+/* Precision variants. Point densities (sf_kde_points, DIRECT, kNN bandwidths):
+ * the squared-distance cross term on tensor cores in TF32 (one pass), 3xTF32
+ * (hi/lo split, three passes) or BF16 (one pass, 8 significant bits); see
+ * sf_kde_points. Grids (sf_kde_grid, truncated Gaussian, kNN or fixed lengths):
+ * the particles whose support covers a whole 8 x 4 x 8 node tile are summed as
+ * a tensor-core product of their per-axis kernel factors in the same three
+ * forms (terms off by about 1e-3 relative in TF32, 8e-3 in BF16, 2^-21 in
+ * 3xTF32); the other particles stay FP32. FP32 is the default everywhere and
+ * the only form of batches and of every other call. */
 enum { SF_PREC_FP32 = 0, SF_PREC_TF32 = 1, SF_PREC_3XTF32 = 2, SF_PREC_BF16 = 3 };
 
 /* Point densities: DIRECT evaluates the kernel sum at each point (self term
@@ -337,7 +341,8 @@ sf_status sf_count_support_pairs(sf_index *idx, const sf_box *roi, const int32_t
  *   [0] in-support (node, particle) pairs (= h_grid_pairs),
  *   [1] candidate-leaf visits by node tiles,
  *   [2] (particle, tile) pairs staged: particles whose support reaches the tile,
- *   [3] 0 (reserved),
+ *   [3] of those, the pairs whose support covers every node of the tile (summed
+ *       on the tensor cores),
  *   [4] (node, particle) pairs evaluated (every staged particle against every
  *       node of its tile).
  * Synchronises the stream. Rules kNN and fixed.

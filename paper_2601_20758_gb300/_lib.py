@@ -277,12 +277,12 @@ def sf_query_workspace(idx, roi: sf_box, dims, kernel, params, what=SF_WS_GRID, 
 
 def sf_grid_work_counts(idx, roi: sf_box, dims, kernel, params, stream=None) -> dict:
     """Work accounting of one ROI grid: in-support pairs, candidate-leaf visits, staged
-    (particle, tile) pairs, a reserved zero, evaluated pairs."""
+    (particle, tile) pairs, those covering the whole tile, evaluated pairs."""
     d = (_i32 * 3)(*_dims3(dims))
     c = (_i64 * 5)()
     _check("sf_grid_work_counts", load().sf_grid_work_counts(idx, ctypes.byref(roi), d, int(kernel),
                                                              ctypes.byref(params), c, _stream(stream)))
-    keys = ("pairs", "leaf_visits", "staged", "reserved", "evaluated")
+    keys = ("pairs", "leaf_visits", "staged", "full_tile", "evaluated")
     return {k: int(v) for k, v in zip(keys, c)}
 
 

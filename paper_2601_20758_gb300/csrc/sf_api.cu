@@ -269,8 +269,9 @@ sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], i
     if (!idx || !d_out) return fail(SF_ERR_INVALID_ARG, "sf_kde_grid: NULL argument");
     SF_TRY(check_roi(roi, "sf_kde_grid"));
     SF_TRY(check_params(idx, params, kernel, "sf_kde_grid"));
-    if (params->prec != SF_PREC_FP32)
-        return fail(SF_ERR_INVALID_ARG, "sf_kde_grid: grids are FP32 only");
+    if (params->prec != SF_PREC_FP32 && (kernel != SF_K_GAUSS3 || params->rule == SF_BW_MBE))
+        return fail(SF_ERR_INVALID_ARG,
+                    "sf_kde_grid: TF32 / 3xTF32 / BF16 grids need the Gaussian kernel and rule KNN or FIXED");
     GridSpec g;
     SF_TRY(make_grid(*roi, dims, g, "sf_kde_grid"));
     cudaStream_t s = (cudaStream_t)stream;
@@ -279,6 +280,7 @@ sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], i
     SF_TRY_SCRATCH(sc);
     Prepared pr;
     SF_TRY(prepare(idx, *roi, &g, kernel, *params, sc, pr, s));
+    pr.call.prec = params->prec;
     StatusPeek peek;
     peek.d_src = pr.status;
     SF_TRY(density_grid(idx, *roi, g, pr.call, d_out, d_mass, s, nullptr, &peek));

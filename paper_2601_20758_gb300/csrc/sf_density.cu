@@ -636,6 +636,7 @@ __global__ void __launch_bounds__(kGridThreads, 3) k_grid(GridArgs a) {
 // ---------------------------------------------------------------------------
 struct MrArgs {
     EngineArgs e;               // common part (index, bandwidths, kernel constant)
+    int prec;                   // SF_PREC_* of the work kernel (host-side choice)
     const RoiDesc *rois;        // device array
     const int *tile_roi;        // global tile -> ROI index
     int ntiles;
@@ -720,6 +721,65 @@ __global__ void k_grid_items(const uint32_t *__restrict__ cnt, const uint32_t *_
         items[ioff[t] + i] = make_int4(t, (int)(b + i * lpw), (int)(b + min(n, (i + 1) * lpw)), 0);
 }
 
+// ---- tensor-core sums of particles whose support covers the whole tile ------
+// For such a particle every node (x, y, z) of the 8 x 4 x TZ tile is in support
+// and its Gaussian term is the product tx[x] ty[y] tz[z] of its table entries,
+// so the tile's sum over these particles is a matrix product:
+//   rho[(x, y), z] += sum_s A[(x, y), s] B[s, z],  A = tx ty (32 x S),  B = tz (S x 8).
+// It runs as mma.sync m16n8k8 (TF32) or m16n8k16 (BF16) blocks with FP32
+// accumulators; 3xTF32 splits every operand into TF32 hi + lo parts and adds the
+// three products hi*hi + hi*lo + lo*hi (about 2^-21 relative). These are the
+// grid's precision variants; the FP32 path keeps every particle on the FP32
+// pipes, which measured faster on this GPU than these mma.sync blocks.
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_k8_tf32(float d[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                            uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_k16_bf16(float d[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                             uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Two floats as a bf16 pair: `first` in the low half (the lower column / row index).
+__device__ __forceinline__ uint32_t bf16x2_of(float first, float second) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(second), "f"(first));
+    return r;
+}
+
+// A (x = g, y) (TF32 fragment values) times B; PREC 3XTF32 adds the three split products.
+template <int PREC>
+__device__ __forceinline__ void mma_k8(float d[4], float a0, float a1, float a2, float a3, float b0,
+                                       float b1) {
+    const uint32_t A0 = tf32_of(a0), A1 = tf32_of(a1), A2 = tf32_of(a2), A3 = tf32_of(a3);
+    const uint32_t B0 = tf32_of(b0), B1 = tf32_of(b1);
+    if (PREC != SF_PREC_3XTF32) {
+        mma_k8_tf32(d, A0, A1, A2, A3, B0, B1);
+        return;
+    }
+    const uint32_t L0 = tf32_of(a0 - __uint_as_float(A0)), L1 = tf32_of(a1 - __uint_as_float(A1));
+    const uint32_t L2 = tf32_of(a2 - __uint_as_float(A2)), L3 = tf32_of(a3 - __uint_as_float(A3));
+    const uint32_t M0 = tf32_of(b0 - __uint_as_float(B0)), M1 = tf32_of(b1 - __uint_as_float(B1));
+    mma_k8_tf32(d, L0, L1, L2, L3, B0, B1);
+    mma_k8_tf32(d, A0, A1, A2, A3, M0, M1);
+    mma_k8_tf32(d, A0, A1, A2, A3, B0, B1);
+}
+
 // Shared memory of one warp of the split pipeline: its 8 x 4 x TZ node tile.
 template <int TZ>
 struct WTileSmem {
@@ -738,10 +798,14 @@ struct WTileSmem {
 // Persistent warps: each takes (ROI, tile, leaf range) items from a counter and
 // sums them into the item's partial grid. No block barriers: a warp owns its
 // tile, its staging and its tables.
-template <int KER, int BW, bool CLIP, bool CNT, int TZ>
+template <int KER, int BW, bool CLIP, bool CNT, int TZ, int PREC = SF_PREC_FP32>
 __global__ void __launch_bounds__(kGridThreads, 4)
     k_mr_work(MrArgs a, const int4 *__restrict__ items, const uint32_t *__restrict__ n_items,
               const int *__restrict__ list, double *__restrict__ part, unsigned int *next) {
+    // the tensor-core path of the precision variants: Gaussian, 8 nodes deep (the
+    // B operand's 8 columns); the FP32 path sums every particle in FP32
+    constexpr bool kMma = KER == SF_K_GAUSS3 && TZ == 8 && PREC != SF_PREC_FP32;
+    constexpr bool kFull = KER == SF_K_GAUSS3 && TZ == 8 && (PREC != SF_PREC_FP32 || CNT);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WTileSmem<TZ> &S = reinterpret_cast<WTileSmem<TZ> *>(smem_raw)[warp];
@@ -807,7 +871,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
 #pragma unroll
         for (int k = 0; k < TZ; ++k) acc[k] = sum[k] = cmp[k] = 0.f;
         unsigned long long np = 0;
-        unsigned long long st_leaves = 0, st_staged = 0, st_tested = 0;
+        unsigned long long st_leaves = 0, st_staged = 0, st_full = 0, st_tested = 0;
         for (int lb = it.y; lb < it.z; ++lb) {
             // ---- one candidate leaf: refine (footprint in this tile, clip) and stage
             const int64_t i = (int64_t)list[lb] * kLeaf + lane;
@@ -815,6 +879,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
             float l[3] = {0.f, 0.f, 0.f}, rl[3] = {0.f, 0.f, 0.f};
             int2 fp = make_int2(0, 0);
+            bool full = false;  // the support covers every node of the tile
             if (i < E.tv.n) {
                 p = __ldg(&E.tv.pos[i]);
                 point_ell<BW>(E, S.uni, i, p, l);
@@ -886,17 +951,47 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                     fp.x = f0[0] | (f1[0] << 8) | (f0[1] << 16) | (f1[1] << 24);
                     fp.y = f0[2] | (f1[2] << 8);
                 }
+                // Full coverage: q is convex along each axis, so its largest value over the
+                // tile is at a corner node; the node test fl(qx + qy) < fl(qmax - qz) is
+                // monotone in each q, so passing it with the per-axis maxima passes it
+                // at every node (as the table path would evaluate it).
+                if (kFull && acc_pt && f0[0] == 0 && f1[0] == g.nv[0] - 1 && f0[1] == 0 &&
+                    f1[1] == g.nv[1] - 1 && f0[2] == 0 && f1[2] == g.nv[2] - 1) {
+                    const int aoff[3] = {0, kWX, kWX + kWY};
+                    float qm[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const float u = KDef<KER>::uscale * rl[k];
+                        float m = 0.f;
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const float2 nc = S.axt[aoff[k] + (e ? g.nv[k] - 1 : 0)];
+                            const float d = (nc.x - pc[k]) + nc.y;
+                            const float t = d * u;
+                            m = fmaxf(m, t * t);
+                        }
+                        qm[k] = m;
+                    }
+                    full = qm[0] + qm[1] < KDef<KER>::qmax - qm[2];
+                }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, acc_pt);
             const int ns = __popc(bal);
             if (ns == 0) continue;  // warp-uniform
+            // staged slots: the full-coverage particles first, [0, nf); the others [nf, ns)
+            const unsigned balf = __ballot_sync(0xffffffffu, acc_pt && full);
+            const int nf = kMma ? __popc(balf) : 0;
             if (CNT && lane == 0) {
                 ++st_leaves;
                 st_staged += ns;
+                st_full += __popc(balf);
                 st_tested += (unsigned long long)ns * (kWX * kWY * TZ);
             }
+            const unsigned lt = (1u << lane) - 1u;
+            const int my_slot = !kMma ? __popc(bal & lt)
+                                      : (full ? __popc(balf & lt) : nf + __popc(bal & ~balf & lt));
             if (acc_pt) {
-                const int s = __popc(bal & ((1u << lane) - 1u));
+                const int s = my_slot;
                 S.sp[s] = make_float4(p.x, p.y, p.z, E.cnorm * ((rl[0] * rl[1]) * rl[2]));
                 S.su[s] = make_float4(KDef<KER>::uscale * rl[0], KDef<KER>::uscale * rl[1],
                                       KDef<KER>::uscale * rl[2], 0.f);
@@ -914,7 +1009,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
             };
             if (ns >= kLaneTables) {
                 if (acc_pt) {
-                    const int s = __popc(bal & ((1u << lane) - 1u));
+                    const int s = my_slot;
                     const float c = E.cnorm * ((rl[0] * rl[1]) * rl[2]);
                     const float u0 = KDef<KER>::uscale * rl[0], u1 = KDef<KER>::uscale * rl[1],
                                 u2 = KDef<KER>::uscale * rl[2];
@@ -965,7 +1060,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
             __syncwarp();
             {
             // ---- accumulate: lane owns column (cx, cy) and TZ nodes in z
-            for (int s = 0; s < ns; ++s) {
+            for (int s = nf; s < ns; ++s) {
                 const float2 ex = S.tx[s][cx];
                 const float2 ey = S.ty[s][cy];
                 if (KER == SF_K_GAUSS3) {
@@ -990,6 +1085,63 @@ __global__ void __launch_bounds__(kGridThreads, 4)
                 }
             }
             }
+            if (kMma && nf > 0) {  // warp-uniform: the full-coverage particles on the tensor cores
+                const int gq = lane >> 2, tig = lane & 3;
+                float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+                if (PREC == SF_PREC_BF16) {
+                    for (int s0 = 0; s0 < nf; s0 += 16) {
+                        float ax[4], ay[4][4], bz[4];  // particles s0 + 2 tig + {0, 1, 8, 9}
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int sp = s0 + 2 * tig + (e & 1) + 8 * (e >> 1);
+                            const bool v = sp < nf;
+                            ax[e] = v ? S.tx[sp][gq].x : 0.f;
+                            bz[e] = v ? S.tz[sp][gq].x : 0.f;
+#pragma unroll
+                            for (int y = 0; y < 4; ++y) ay[e][y] = v ? S.ty[sp][y].x : 0.f;
+                        }
+                        const uint32_t b0 = bf16x2_of(bz[0], bz[1]), b1 = bf16x2_of(bz[2], bz[3]);
+#pragma unroll
+                        for (int mb = 0; mb < 2; ++mb) {
+                            float *d = mb ? d1 : d0;
+                            const int y0 = 2 * mb, y1 = 2 * mb + 1;
+                            mma_k16_bf16(d, bf16x2_of(ax[0] * ay[0][y0], ax[1] * ay[1][y0]),
+                                         bf16x2_of(ax[0] * ay[0][y1], ax[1] * ay[1][y1]),
+                                         bf16x2_of(ax[2] * ay[2][y0], ax[3] * ay[3][y0]),
+                                         bf16x2_of(ax[2] * ay[2][y1], ax[3] * ay[3][y1]), b0, b1);
+                        }
+                    }
+                } else {
+                    for (int s0 = 0; s0 < nf; s0 += 8) {
+                        const int sa = s0 + tig, sb = s0 + tig + 4;
+                        const bool va = sa < nf, vb = sb < nf;
+                        const float txa = va ? S.tx[sa][gq].x : 0.f, txb = vb ? S.tx[sb][gq].x : 0.f;
+                        const float tza = va ? S.tz[sa][gq].x : 0.f, tzb = vb ? S.tz[sb][gq].x : 0.f;
+#pragma unroll
+                        for (int mb = 0; mb < 2; ++mb) {
+                            const float ya0 = va ? S.ty[sa][2 * mb].x : 0.f, ya1 = va ? S.ty[sa][2 * mb + 1].x : 0.f;
+                            const float yb0 = vb ? S.ty[sb][2 * mb].x : 0.f, yb1 = vb ? S.ty[sb][2 * mb + 1].x : 0.f;
+                            mma_k8<PREC>(mb ? d1 : d0, txa * ya0, txa * ya1, txb * yb0, txb * yb1, tza, tzb);
+                        }
+                    }
+                }
+                // to the column owners: row r = x + 8 y of the product is lane r's column
+                float *cb = reinterpret_cast<float *>(S.tx);  // the tables are no longer read
+                __syncwarp();
+#pragma unroll
+                for (int mb = 0; mb < 2; ++mb) {
+                    const float *d = mb ? d1 : d0;
+                    const int r0 = 16 * mb + gq;
+                    cb[r0 * 8 + 2 * tig] = d[0];
+                    cb[r0 * 8 + 2 * tig + 1] = d[1];
+                    cb[(r0 + 8) * 8 + 2 * tig] = d[2];
+                    cb[(r0 + 8) * 8 + 2 * tig + 1] = d[3];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < TZ; ++k) acc[k] += cb[lane * 8 + k];
+                if (CNT && cx < g.nv[0] && cy < g.nv[1]) np += (unsigned long long)nf * g.nv[2];
+            }
             __syncwarp();
             fold<TZ>(acc, sum, cmp);
         }
@@ -997,6 +1149,7 @@ __global__ void __launch_bounds__(kGridThreads, 4)
         if (CNT && lane == 0) {  // work accounting of the counting variant
             atomicAdd(a.pairs + 1, st_leaves);
             atomicAdd(a.pairs + 2, st_staged);
+            atomicAdd(a.pairs + 3, st_full);
             atomicAdd(a.pairs + 4, st_tested);
         }
         double *o = part + ((int64_t)item * 32 + lane) * TZ;
@@ -1169,6 +1322,16 @@ struct MrBuffers {
     int64_t slots;        // resident blocks of k_mr_work
 };
 
+template <int KER, int BW, bool CLIP, bool CNT, int TZ, int PREC>
+static sf_status launch_work(const MrArgs &a, const MrBuffers &b, cudaStream_t s) {
+    static std::atomic<uint64_t> attr{0};
+    SF_TRY_CUDA(smem_attr_once(k_mr_work<KER, BW, CLIP, CNT, TZ, PREC>, mr_work_smem<TZ>(), attr));
+    SF_TRY_CUDA(launch(k_mr_work<KER, BW, CLIP, CNT, TZ, PREC>, dim3((unsigned)b.slots), dim3(kGridThreads),
+                       mr_work_smem<TZ>(), s, a, (const int4 *)b.items, (const uint32_t *)(b.tot + 1),
+                       (const int *)b.list, b.part, b.next));
+    return SF_OK;
+}
+
 // Execution: list, items, persistent work, ordered reduce (no host sync; capturable).
 template <int KER, int BW, bool CLIP, bool CNT, int TZ>
 static sf_status mr_exec(const MrArgs &a, const MrBuffers &b, cudaStream_t s) {
@@ -1184,9 +1347,17 @@ static sf_status mr_exec(const MrArgs &a, const MrBuffers &b, cudaStream_t s) {
     SF_TRY_CUDA(cudaMemsetAsync(b.next, 0, sizeof(unsigned int), s));
     {
         KTimer t(CNT ? "k_grid_work_count" : "k_grid_work", s);
-        SF_TRY_CUDA(launch(k_mr_work<KER, BW, CLIP, CNT, TZ>, dim3((unsigned)b.slots), dim3(kGridThreads),
-                           mr_work_smem<TZ>(), s, a, (const int4 *)b.items,
-                           (const uint32_t *)(b.tot + 1), (const int *)b.list, b.part, b.next));
+        bool done = false;
+        if constexpr (KER == SF_K_GAUSS3 && TZ == 8 && !CNT && BW != BW_ANISO) {
+            done = true;
+            switch (a.prec) {
+                case SF_PREC_TF32: SF_TRY((launch_work<KER, BW, CLIP, CNT, TZ, SF_PREC_TF32>(a, b, s))); break;
+                case SF_PREC_3XTF32: SF_TRY((launch_work<KER, BW, CLIP, CNT, TZ, SF_PREC_3XTF32>(a, b, s))); break;
+                case SF_PREC_BF16: SF_TRY((launch_work<KER, BW, CLIP, CNT, TZ, SF_PREC_BF16>(a, b, s))); break;
+                default: done = false;
+            }
+        }
+        if (!done) SF_TRY((launch_work<KER, BW, CLIP, CNT, TZ, SF_PREC_FP32>(a, b, s)));
     }
     SF_TRY_CUDA(launch(k_mr_reduce<TZ>, dim3(blocks_for(a.ntiles, kGridThreads / 32)), dim3(kGridThreads), 0, s, a,
                        (const uint32_t *)b.ic, (const uint32_t *)b.ioff, (const double *)b.part));
@@ -1366,6 +1537,7 @@ static sf_status density_grid_impl(sf_index *idx, const sf_box &roi, const GridS
     a.tile_roi = tile_roi;
     a.ntiles = (int)tiles;
     a.pairs = d_pairs;
+    a.prec = call.prec;
     {
         KTimer t(d_pairs ? "k_grid_count" : "k_grid", s);
         if (call.kernel == SF_K_EPAN)
@@ -1591,6 +1763,7 @@ sf_status batch_create(sf_index *idx, int nroi, const sf_box *rois, const GridSp
     P->a.tile_roi = (const int *)p_tr;
     P->a.ntiles = (int)ntiles;
     P->a.pairs = nullptr;
+    P->a.prec = SF_PREC_FP32;
     P->b.cnt = (uint32_t *)p_cnt;
     P->b.off = (uint32_t *)p_off;
     P->b.tot = (uint32_t *)p_tot;

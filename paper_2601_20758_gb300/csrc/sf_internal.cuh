@@ -298,6 +298,7 @@ struct DensityCall {
     const float4 *ell;  // BW_ANISO per sorted point (lx, ly, lz, unused); else null
     const DensityParams *dp;  // device
     float4 *nell_override;     // node max-ell array to use (null: the index's own)
+    int prec = SF_PREC_FP32;   // grids: SF_PREC_* (non-FP32: Gaussian with kNN or fixed lengths)
 };
 
 // peek (nullable): a status word read back at the call's sizing synchronisation.

@@ -93,7 +93,69 @@ def test_tensor_core_rejected_where_not_defined():
         with pytest.raises(L.SFError):
             L.sf_kde_points(idx, L.make_box((0, 0, 0), (1, 1, 1)), None, L.SF_K_GAUSS3, p, dens, ids)
         grid = torch.empty(8 ** 3, device="cuda")
-        with pytest.raises(L.SFError):
-            L.sf_kde_grid(idx, L.make_box((0, 0, 0), (1, 1, 1)), (8, 8, 8), L.SF_K_GAUSS3, p, grid)
+        with pytest.raises(L.SFError):   # the grid variants are Gaussian only
+            L.sf_kde_grid(idx, L.make_box((0, 0, 0), (1, 1, 1)), (8, 8, 8), L.SF_K_EPAN, p, grid)
+        with pytest.raises(L.SFError):   # batches are FP32 only
+            L.sf_batch_kde_grid(idx, [L.make_box((0, 0, 0), (1, 1, 1))], [(8, 8, 8)], L.SF_K_GAUSS3, p,
+                                [grid])
+    finally:
+        L.sf_free_index(idx)
+
+
+# Grid variants: the particles whose support covers a whole 8 x 4 x 8 node tile are
+# summed as a tensor-core product of their per-axis factors (the others stay FP32).
+# A priori: TF32 rounds the two operands A = tx ty and B = tz to 11 significant bits,
+# so each such term is off by up to about 2 * 2^-11 = 1e-3 relative; BF16 (8 bits)
+# by 2 * 2^-8 = 8e-3; 3xTF32 by about 2^-21. Roundings of different terms partly
+# cancel: measured on this cloud and ROI (GB300), max / rms relative: FP32 1.1e-7 /
+# 2.9e-8, 3xTF32 3.1e-7 / 1.8e-7, TF32 5.7e-5 / 1.5e-5, BF16 4.9e-4 / 1.2e-4.
+GRID_BOUNDS = {"fp32": 1e-5, "3xtf32": 3e-6, "tf32": 5e-4, "bf16": 4e-3}
+GRID_RMS = {"fp32": 1e-6, "3xtf32": 2e-6, "tf32": 1.5e-4, "bf16": 1.2e-3}
+
+
+def test_tensor_core_grid_variants_error():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_20758_gb300 import build
+    build.build()
+    from paper_2601_20758_gb300 import _lib as L
+    xyz = synth.plain_cloud(20000, seed=23)
+    n = xyz.shape[0]
+    roi = ((0.40, 0.42, 0.45), (0.52, 0.55, 0.56))   # a zoom: supports cover whole node tiles
+    dims = (33, 30, 27)
+    d = torch.from_numpy(xyz).cuda()
+    idx = L.sf_build_index(d)
+    report = {}
+    try:
+        p = L.make_params(rule=L.SF_BW_KNN, k=32)
+        L.sf_bandwidths(idx, p)
+        work = L.sf_grid_work_counts(idx, L.make_box(*roi), dims, L.SF_K_GAUSS3, p)
+        assert work["full_tile"] > 0.5 * work["staged"], work
+        h, _, _ = oracle.knn(xyz, 32)
+        ref = oracle.kde_grid(xyz, oracle.iso_ell(h), roi, dims, oracle.GAUSS3, oracle.SCOPE_GLOBAL)
+        r = ref["rho"]
+        big = r >= 1e-3 * r.max()
+        G = dims[0] * dims[1] * dims[2]
+        for name, prec in (("fp32", L.SF_PREC_FP32), ("3xtf32", L.SF_PREC_3XTF32),
+                           ("tf32", L.SF_PREC_TF32), ("bf16", L.SF_PREC_BF16)):
+            q = L.make_params(rule=L.SF_BW_KNN, k=32)
+            q.prec = prec
+            out = torch.empty(G, device="cuda")
+            L.sf_kde_grid(idx, L.make_box(*roi), dims, L.SF_K_GAUSS3, q, out)
+            again = torch.empty(G, device="cuda")
+            L.sf_kde_grid(idx, L.make_box(*roi), dims, L.SF_K_GAUSS3, q, again)
+            assert torch.equal(out, again), name           # deterministic
+            g = out.cpu().numpy().astype(np.float64)
+            excess = np.maximum(np.abs(g - r) - ref["amb"], 0.0)
+            rel = excess[big] / r[big]
+            report[name] = {"max_rel": float(rel.max()), "rms_rel": float(np.sqrt(np.mean(rel ** 2)))}
+        out = os.environ.get("SF_TENSOR_REPORT")
+        if out:
+            with open(out, "a") as f:
+                f.write(json.dumps({"grid": True, **report}) + "\n")
+        for name, rep in report.items():
+            assert rep["max_rel"] <= GRID_BOUNDS[name], (name, rep)
+            assert rep["rms_rel"] <= GRID_RMS[name], (name, rep)
+        assert report["3xtf32"]["max_rel"] < report["tf32"]["max_rel"] < report["bf16"]["max_rel"]
     finally:
         L.sf_free_index(idx)
