@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-nested", action="store_true", help="skip the nested 16.8M-point legs")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
+    ap.add_argument("--no-baselines", action="store_true",
+                    help="skip the precomputed-field (PS / PM) comparison")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-vs-plain comparison over 64 uneven ROIs")
     ap.add_argument("--no-prec", action="store_true",
@@ -487,6 +489,7 @@ def run_large(ctx):
 
         flat = sorted(x for r in roi_ms for x in r)
         e2e = None if args.no_e2e else run_e2e_large(ctx, idx, boxes, p, grids, sum(pairs))
+        baselines = None if args.no_baselines else run_baselines(ctx, idx, p, rois, grids, roi_ms)
         serving = None if args.no_serve else run_serving(ctx, idx, n, p, rois)
     finally:
         L.sf_free_index(idx)
@@ -519,7 +522,45 @@ def run_large(ctx):
             "k_grid_work_ms_per_roi": per_roi_work,
             "setup": setup, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "serving": serving,
+            "precomputed_fields": baselines,
             "cosmology_16M": nested}
+
+
+def run_baselines(ctx, idx, p, rois, grids, roi_ms):
+    """The paper's study conditions on the zoom ROIs: PS (one 64^3 field) and PM (64^3 and
+    128^3 fields blended by the scale, S = ROI edge, S_min = 1e-3, S_max = 1) read at each
+    ROI's 256^3 nodes, against the dynamic recompute (DR, the grids of the timed steps):
+    view time (CUDA events) and relative L2 distance from the DR grid."""
+    from paper_2601_20758_gb300.fields import PrecomputedFields
+    L, torch, stream = ctx["L"], ctx["torch"], ctx["stream"]
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    pf = PrecomputedFields(idx, p, L.SF_K_GAUSS3, resolutions=(64, 128), stream=stream)
+    z.record(stream)
+    torch.cuda.synchronize()
+    out = {"fields_ms": a.elapsed_time(z), "rois": []}
+    view = torch.empty_like(grids[0])
+    for i, (lo, hi) in enumerate(rois):
+        ent = {"edge": float(hi[0] - lo[0]), "dr_ms_median": statistics.median(roi_ms[i])}
+        dr = grids[i].double()
+        nrm = float(torch.linalg.vector_norm(dr))
+        for name in ("ps", "pm"):
+            ms = []
+            for _ in range(3):
+                a.record(stream)
+                if name == "ps":
+                    pf.ps_view((lo, hi), LARGE_DIMS, view, stream=stream)
+                else:
+                    pf.pm_view((lo, hi), LARGE_DIMS, float(hi[0] - lo[0]), 1e-3, 1.0, view, stream=stream)
+                z.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(z))
+            ent[f"{name}_ms"] = sorted(ms)[1]
+            ent[f"{name}_rel_l2_vs_dr"] = float(torch.linalg.vector_norm(view.double() - dr)) / max(nrm, 1e-300)
+        out["rois"].append(ent)
+    del pf
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e_large(ctx, idx, boxes, p, grids, pairs_step):
@@ -558,28 +599,43 @@ def run_serving(ctx, idx, n, p, rois):
     args, L, torch = ctx["args"], ctx["L"], ctx["torch"]
     lo, hi = rois[-1]
     centre = [(float(lo[k]) + float(hi[k])) / 2 for k in range(3)]
-    reqs = serve.navigation_requests(args.serve_requests, rate=args.serve_rate, centre=centre,
-                                     seed=2601)
     free, _ = torch.cuda.mem_get_info()
     slots = args.serve_slots
-    ex = serve.GpuExecutor(idx, p, L.SF_K_GAUSS3, n, slots=slots, max_nodes=256 ** 3, max_points=1)
-    srv = serve.Server(ex, slots=slots, mem_budget=int(0.5 * free))
-    try:
-        warm = [serve.Request(-1 - i, r.lo, r.hi, r.dims, want_points=r.want_points, prec=r.prec)
-                for i, r in enumerate(reqs[:2 * slots])]
-        srv.replay(warm)
-        srv.completed.clear()
-        st = srv.replay(reqs)
-    finally:
-        srv.close()
-    ok = [r for r in srv.completed if r.status == "done"]
-    st["service_p99_by_grid_edge_ms"] = {
-        str(e): percentile(sorted(1e3 * (r.done - r.admitted) for r in ok if r.dims[0] == e), 99)
-        for e in (64, 96, 128, 192, 256)}
+
+    def replay(cache):
+        reqs = serve.navigation_requests(args.serve_requests, rate=args.serve_rate, centre=centre,
+                                         seed=2601, bf16_share=0.3)
+        ex = serve.GpuExecutor(idx, p, L.SF_K_GAUSS3, n, slots=slots, max_nodes=256 ** 3, max_points=1,
+                               cache=cache)
+        srv = serve.Server(ex, slots=slots, mem_budget=int(0.4 * free))
+        try:
+            warm = [serve.Request(-1 - i, r.lo, r.hi, r.dims, want_points=False, prec=r.prec)
+                    for i, r in enumerate(reqs[:2 * slots])]
+            srv.replay(warm)
+            srv.completed.clear()
+            if cache is not None:
+                cache.entry, cache.hits, cache.misses = None, 0, 0
+            st = srv.replay(reqs)
+        finally:
+            srv.close()
+        ok = [r for r in srv.completed if r.status == "done"]
+        st["service_p99_by_grid_edge_ms"] = {
+            str(e): percentile(sorted(1e3 * (r.done - r.admitted) for r in ok if r.dims[0] == e), 99)
+            for e in (64, 96, 128, 192, 256)}
+        if cache is not None:
+            st["cache"] = {"hits": cache.hits, "misses": cache.misses, "margin": cache.margin,
+                           "coarsen_tol": cache.tol}
+        del ex
+        torch.cuda.empty_cache()
+        return st
+
+    st = replay(None)
+    st["with_view_cache"] = replay(serve.ViewCache(margin=0.25, coarsen_tol=0.3, max_nodes=384 ** 3))
     st["rate_per_s"] = args.serve_rate
     st["stream"] = ("Poisson arrivals over the 1.07B-point cloud, zoom walk over log10 edge in "
                     "[-3, 0] (sigma 0.1 decade), pan <= half an edge, grid edge in "
-                    "{64, 96, 128, 192, 256}^3; every request recomputes the ROI grid (FP32)")
+                    "{64, 96, 128, 192, 256}^3; every request recomputes the ROI grid; 30% of the "
+                    "requests in BF16 (tensor-core grid variant), 70% FP32")
     return st
 
 

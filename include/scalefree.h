@@ -255,6 +255,26 @@ sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids
                     uint32_t *d_sel_ids, int64_t *h_nsel, double *h_threshold, void *stream);
 
 /*
+ * sf_resample_grid -- a finished grid read at the nodes of another grid by
+ * trilinear interpolation (Sec. 3.1, last step: the density at any position
+ * inside B from the eight nodes around it).
+ *
+ * d_src: device float [src_dims[2]][src_dims[1]][src_dims[0]] over the closed box
+ * src_box (vertex-centred nodes, x fastest, as sf_kde_grid writes it). Every node
+ * of the grid (dst_box, dst_dims) gets weight * the interpolated value, stored
+ * into d_dst (device float, same layout) or, with accumulate != 0, added to
+ * what d_dst holds (so w1 F1 + w2 F2 takes two calls). Node positions and the
+ * weighted sum are computed in FP64, rounded once to float. Destination nodes
+ * outside src_box get 0 (or nothing added); *h_outside (host, nullable) receives
+ * their number and then the stream is synchronised. For view caches (a small pan
+ * or zoom answered from a grid over a larger box) and for precomputed global
+ * fields read at a view's nodes. Errors: INVALID_ARG, OOM, CUDA.
+ */
+sf_status sf_resample_grid(const float *d_src, const sf_box *src_box, const int32_t src_dims[3],
+                           const sf_box *dst_box, const int32_t dst_dims[3], float weight,
+                           int32_t accumulate, float *d_dst, int64_t *h_outside, void *stream);
+
+/*
  * Batched ROI grids: many ROIs of uneven size in one persistent execution.
  *
  * Every (ROI, 8x4xZ node tile) lists its candidate leaves, the lists are cut

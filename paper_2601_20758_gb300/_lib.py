@@ -107,6 +107,9 @@ _PROTOS = {
     "sf_query_workspace": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
                                           ctypes.POINTER(sf_params), _i32, ctypes.POINTER(_i64), _vp]),
     "sf_last_call_workspace": (_i64, []),
+    "sf_resample_grid": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32),
+                                        ctypes.POINTER(sf_box), ctypes.POINTER(_i32), ctypes.c_float,
+                                        _i32, _vp, ctypes.POINTER(_i64), _vp]),
     "sf_kernel_timing_enable": (None, [ctypes.c_int]),
     "sf_kernel_timing_reset": (None, []),
     "sf_kernel_timing": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
@@ -284,6 +287,23 @@ def sf_grid_work_counts(idx, roi: sf_box, dims, kernel, params, stream=None) -> 
                                                              ctypes.byref(params), c, _stream(stream)))
     keys = ("pairs", "leaf_visits", "staged", "full_tile", "evaluated")
     return {k: int(v) for k, v in zip(keys, c)}
+
+
+def sf_resample_grid(d_src, src_box: sf_box, src_dims, dst_box: sf_box, dst_dims, d_dst,
+                     weight=1.0, accumulate=False, want_outside=False, stream=None):
+    """d_dst (= or +=) weight * trilinear interpolation of the grid d_src at the nodes of
+    (dst_box, dst_dims); returns the number of destination nodes outside src_box when
+    want_outside (this synchronises the stream)."""
+    sd, dd = _dims3(src_dims), _dims3(dst_dims)
+    ps = _dev_buf(d_src, "d_src", "f32", max(sd[0], 0) * max(sd[1], 0) * max(sd[2], 0))
+    pd = _dev_buf(d_dst, "d_dst", "f32", max(dd[0], 0) * max(dd[1], 0) * max(dd[2], 0))
+    o = _i64(0)
+    _check("sf_resample_grid", load().sf_resample_grid(ps, ctypes.byref(src_box), (_i32 * 3)(*sd),
+                                                       ctypes.byref(dst_box), (_i32 * 3)(*dd),
+                                                       float(weight), 1 if accumulate else 0, pd,
+                                                       ctypes.byref(o) if want_outside else None,
+                                                       _stream(stream)))
+    return int(o.value) if want_outside else None
 
 
 def sf_last_call_workspace() -> int:

@@ -22,6 +22,8 @@ extern std::atomic<uint64_t> g_launches;
 
 // Records a message for sf_last_error() and returns st.
 sf_status fail(sf_status st, const char *fmt, ...);
+// Every entry point starts with this: clears the message, opens the scratch count.
+void clear_error();
 
 #define SF_TRY_CUDA(expr)                                                                    \
     do {                                                                                     \

@@ -190,13 +190,61 @@ class Server:
                 "slots": self.slots, "budget_bytes": self.budget}
 
 
+class ViewCache:
+    """Recompute trigger with a viewport-plus-margin cache.
+
+    The paper recomputes the density whenever the view changes and names, as
+    future work, a threshold below which a change triggers no recompute and a
+    density computed for the visible region plus a margin. Here: a grid request
+    is a hit when the cached grid's box covers the requested box and its node
+    spacing is at most (1 + coarsen_tol) times the requested one on every axis;
+    the view is then read from the cached grid by trilinear interpolation
+    (sf_resample_grid). A miss computes the requested box widened on every side
+    by `margin` of its extent, at the requested spacing -- the requested nodes are
+    nodes of the widened grid, so the missing request itself is answered
+    exactly -- and that grid becomes the cached one.
+    """
+
+    def __init__(self, margin: float = 0.25, coarsen_tol: float = 0.3, max_nodes: int = 400 ** 3):
+        self.margin, self.tol, self.max_nodes = float(margin), float(coarsen_tol), int(max_nodes)
+        self.entry = None          # (lo, hi, dims, handle)
+        self.hits = self.misses = 0
+
+    @staticmethod
+    def spacing(lo, hi, dims):
+        return tuple((hi[k] - lo[k]) / (dims[k] - 1) for k in range(3))
+
+    def covers(self, lo, hi, dims) -> bool:
+        if self.entry is None:
+            return False
+        clo, chi, cdims, _ = self.entry
+        if any(lo[k] < clo[k] or hi[k] > chi[k] for k in range(3)):
+            return False
+        cs, rs = self.spacing(clo, chi, cdims), self.spacing(lo, hi, dims)
+        return all(cs[k] <= (1.0 + self.tol) * rs[k] for k in range(3))
+
+    def plan(self, lo, hi, dims):
+        """The widened box and node counts of a miss: m = ceil(margin (d - 1)) more nodes
+        on each side at the requested spacing (no widening if that would pass max_nodes)."""
+        sp = self.spacing(lo, hi, dims)
+        m = [int(math.ceil(self.margin * (dims[k] - 1))) for k in range(3)]
+        d2 = [int(dims[k]) + 2 * m[k] for k in range(3)]
+        if d2[0] * d2[1] * d2[2] > self.max_nodes or max(d2) > 4096:
+            return tuple(lo), tuple(hi), tuple(int(v) for v in dims)
+        lo2 = tuple(lo[k] - m[k] * sp[k] for k in range(3))
+        hi2 = tuple(hi[k] + m[k] * sp[k] for k in range(3))
+        return lo2, hi2, tuple(d2)
+
+
 class GpuExecutor:
     """Runs a request through the C ABI on the slot's own CUDA stream. Output
     buffers are preallocated per slot (max_nodes grid nodes, max_points ROI points);
-    admission sizes each request by the library's own workspace figure."""
+    admission sizes each request by the library's own workspace figure. With a
+    ViewCache, grid-only requests go through it (cache buffers: slots + 1, so a
+    miss always finds one that no request is reading)."""
 
     def __init__(self, idx, params, kernel, n_points, slots, max_nodes, max_points=None,
-                 copy_back=False):
+                 copy_back=False, cache: ViewCache | None = None):
         import torch
         from . import _lib as L
         self.L, self.torch = L, torch
@@ -211,23 +259,62 @@ class GpuExecutor:
         cap = n_points if max_points is None else int(max_points)
         dev = "cuda"
         self.grid = [torch.empty(max_nodes, device=dev) for _ in range(slots)]
+        self.cache = cache
+        self._clock = threading.Lock()
+        if cache is not None:
+            self._cbuf = [torch.empty(cache.max_nodes, device=dev) for _ in range(slots + 1)]
+            self._cref = [0] * (slots + 1)
         self.dens = [torch.empty(cap, device=dev) for _ in range(slots)]
         self.ids = [torch.empty(cap, dtype=torch.int32, device=dev) for _ in range(slots)]
         self.sel = [torch.empty(cap, dtype=torch.int32, device=dev) for _ in range(slots)]
 
     def workspace(self, req: Request) -> int:
         """Device bytes the request's calls allocate at most at once (the calls run one
-        after the other on the slot's stream, so the larger of the two)."""
+        after the other on the slot's stream, so the larger of the two; with a view
+        cache, a grid request is sized as a miss: its widened grid)."""
         L = self.L
-        box = L.make_box(req.lo, req.hi)
+        lo, hi, dims = req.lo, req.hi, req.dims
+        if self.cache is not None and not req.want_points:
+            lo, hi, dims = self.cache.plan(lo, hi, dims)
+        box = L.make_box(lo, hi)
         with self._qlock:
-            g = L.sf_query_workspace(self.idx, box, req.dims, self.kernel, self.params["fp32"],
+            g = L.sf_query_workspace(self.idx, box, dims, self.kernel, self.params[req.prec],
                                      L.SF_WS_GRID, stream=self.query_stream)
+            box = L.make_box(req.lo, req.hi)
             p = 0
             if req.want_points:
                 p = L.sf_query_workspace(self.idx, box, req.dims, self.kernel, self.params[req.prec],
                                          L.SF_WS_POINTS, stream=self.query_stream)
         return max(g, p)
+
+    def _cached_grid(self, req: Request, grid, st):
+        """The request's grid through the view cache; returns True on a hit."""
+        L, c = self.L, self.cache
+        with self._clock:
+            hit = c.covers(req.lo, req.hi, req.dims)
+            if hit:
+                lo2, hi2, d2, b = c.entry
+                c.hits += 1
+            else:
+                lo2, hi2, d2 = c.plan(req.lo, req.hi, req.dims)
+                b = next(i for i in range(len(self._cbuf))
+                         if self._cref[i] == 0 and (c.entry is None or c.entry[3] != i))
+                c.misses += 1
+            self._cref[b] += 1
+        try:
+            src = self._cbuf[b][:d2[0] * d2[1] * d2[2]]
+            if not hit:
+                L.sf_kde_grid(self.idx, L.make_box(lo2, hi2), d2, self.kernel, self.params[req.prec],
+                              src, stream=st)
+            L.sf_resample_grid(src, L.make_box(lo2, hi2), d2, L.make_box(req.lo, req.hi), req.dims,
+                               grid, stream=st)
+            st.synchronize()
+        finally:
+            with self._clock:
+                self._cref[b] -= 1
+                if not hit:
+                    c.entry = (lo2, hi2, d2, b)
+        return hit
 
     def run(self, req: Request, slot: int):
         L, torch = self.L, self.torch
@@ -235,8 +322,11 @@ class GpuExecutor:
         box = L.make_box(req.lo, req.hi)
         G = int(req.dims[0]) * int(req.dims[1]) * int(req.dims[2])
         grid = self.grid[slot][:G]
-        L.sf_kde_grid(self.idx, box, req.dims, self.kernel, self.params["fp32"], grid, stream=st)
         out = {"nodes": G}
+        if self.cache is not None and not req.want_points:
+            out["cache_hit"] = self._cached_grid(req, grid, st)
+        else:
+            L.sf_kde_grid(self.idx, box, req.dims, self.kernel, self.params[req.prec], grid, stream=st)
         if req.want_points:
             cnt = L.sf_kde_points(self.idx, box, None, self.kernel, self.params[req.prec],
                                   self.dens[slot], self.ids[slot], stream=st)
