@@ -411,3 +411,109 @@ def select(density, ids, threshold=None, percentile=None):
         t = d.dtype.type(threshold)
     sel = np.sort(ids[d > t])
     return t, sel
+
+
+# ---------------------------------------------------------------------------
+# Selection volume (Sec. 4.1: a density threshold, an iso-surface of the density
+# field computed on the GPU, and the points inside the enclosed volume)
+# ---------------------------------------------------------------------------
+# Every grid cell (x fastest, then y, then z) is split into six tetrahedra that
+# share the cell's diagonal from its lowest corner (0,0,0) to (1,1,1): for each
+# ordering (a, b, c) of the axes, the tetrahedron 0, e_a, e_a + e_b, (1,1,1).
+# Over these tetrahedra the grid values define a continuous piecewise-linear
+# field (neighbouring cells split their shared faces the same way); the
+# selection volume is where it exceeds the threshold t, and its boundary is a
+# triangle mesh (one triangle where one vertex of a tetrahedron lies on the other
+# side from the three others, two where two and two). Orderings in this order:
+TET_ORDERS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def _tet_corners(order):
+    """The four corners (0/1 offsets along x, y, z) of the tetrahedron of one axis ordering."""
+    v = [0, 0, 0]
+    out = [tuple(v)]
+    for ax in order:
+        v[ax] = 1
+        out.append(tuple(v))
+    return out
+
+
+def tet_linear(grid, box, dims, pts):
+    """The piecewise-linear field at positions inside B: the cell by floor((y - lo)/s)
+    clamped to [0, res - 2], local coordinates u in [0, 1]^3, the tetrahedron of the
+    axis ordering with u_a >= u_b >= u_c, and f = f0 + u_a (f1 - f0) + u_b (f2 - f1)
+    + u_c (f3 - f2) along its corners 0, e_a, e_a + e_b, (1,1,1)."""
+    g = np.asarray(grid, dtype=np.float64).reshape(int(dims[2]), int(dims[1]), int(dims[0]))
+    lo = np.asarray(box[0], dtype=np.float64)
+    _, s = grid_axes(box, dims)
+    p = np.asarray(pts, dtype=np.float64).reshape(-1, 3)
+    v = (p - lo) / s
+    c = np.floor(v).astype(np.int64)
+    for k in range(3):
+        c[:, k] = np.clip(c[:, k], 0, int(dims[k]) - 2)
+    u = v - c
+    out = np.empty(p.shape[0])
+    for i in range(p.shape[0]):
+        order = sorted(range(3), key=lambda k: (-u[i, k], k))   # descending, ties by axis
+        corners = _tet_corners(order)
+        f = [g[c[i, 2] + dz, c[i, 1] + dy, c[i, 0] + dx] for dx, dy, dz in corners]
+        ua, ub, uc = u[i, order[0]], u[i, order[1]], u[i, order[2]]
+        out[i] = f[0] + ua * (f[1] - f[0]) + ub * (f[2] - f[1]) + uc * (f[3] - f[2])
+    return out
+
+
+def iso_surface(grid, box, dims, t):
+    """Triangles of the boundary of {piecewise-linear field > t}, in cell order (x
+    fastest), then tetrahedron order (TET_ORDERS), then the case's triangles.
+
+    In a tetrahedron with corners P_i and values f_i, "inside" corners have f_i > t.
+    A crossing on the edge (P_a, P_b) (one inside, one not) is at
+    P_a + (t - f_a) / (f_b - f_a) (P_b - P_a). One inside corner I (or one outside
+    corner O): the triangle of the crossings on I's (O's) three edges, taken in the
+    order of the other corners' indices. Two and two (inside I < J, outside K < L):
+    the quad of crossings IK, IL, JL, JK, as triangles (IK, IL, JL) and (IK, JL, JK).
+    Each triangle is oriented so that its normal (b - a) x (c - a) points away from
+    the inside corners' centroid (outward: toward lower density).
+    Returns float64 [ntri, 3, 3]."""
+    g = np.asarray(grid, dtype=np.float64).reshape(int(dims[2]), int(dims[1]), int(dims[0]))
+    (ax, ay, az), _ = grid_axes(box, dims)
+    tris = []
+    for cz in range(int(dims[2]) - 1):
+        for cy in range(int(dims[1]) - 1):
+            for cx in range(int(dims[0]) - 1):
+                for order in TET_ORDERS:
+                    corners = _tet_corners(order)
+                    P = [np.array([ax[cx + dx], ay[cy + dy], az[cz + dz]]) for dx, dy, dz in corners]
+                    f = [g[cz + dz, cy + dy, cx + dx] for dx, dy, dz in corners]
+                    ins = [i for i in range(4) if f[i] > t]
+                    if len(ins) in (0, 4):
+                        continue
+                    outs = [i for i in range(4) if i not in ins]
+
+                    def cross(a, b):
+                        w = (t - f[a]) / (f[b] - f[a])
+                        return P[a] + w * (P[b] - P[a])
+
+                    if len(ins) == 1 or len(ins) == 3:
+                        lone = ins[0] if len(ins) == 1 else outs[0]
+                        others = [i for i in range(4) if i != lone]
+                        cand = [[cross(lone, o) for o in others]]
+                    else:
+                        i, j = ins
+                        k, l = outs
+                        cand = [[cross(i, k), cross(i, l), cross(j, l)],
+                                [cross(i, k), cross(j, l), cross(j, k)]]
+                    cen = sum(P[i] for i in ins) / len(ins)
+                    for a, b, c in cand:
+                        n = np.cross(b - a, c - a)
+                        if np.dot(n, a - cen) < 0:   # points toward the inside: flip
+                            b, c = c, b
+                        tris.append(np.stack([a, b, c]))
+    return np.array(tris).reshape(-1, 3, 3)
+
+
+def mesh_volume(tris):
+    """Volume enclosed by an oriented closed triangle mesh (divergence theorem):
+    sum over triangles of a . (b x c) / 6."""
+    t = np.asarray(tris, dtype=np.float64)
+    return float(np.sum(np.einsum("ij,ij->i", t[:, 0], np.cross(t[:, 1], t[:, 2]))) / 6.0)

@@ -514,3 +514,78 @@ def test_density_knn_tree_matches_brute_force_bit_for_bit(name, k, kernel, band)
     for key in ("rho", "wpeak", "amb", "pairs"):
         assert np.array_equal(got[key], ref[key]), (key, np.nonzero(got[key] != ref[key])[0][:5])
     assert int(ref["pairs"].sum()) > 0
+
+
+# --------------------------------------------------------------------------
+# Selection volume: the piecewise-linear field and its iso-surface
+# --------------------------------------------------------------------------
+def _field(fn, box, dims):
+    nodes = oracle.grid_nodes(box, dims)
+    return fn(nodes)
+
+
+def test_tet_linear_reproduces_linear_fields_and_nodes():
+    """On a linear field the piecewise-linear interpolant is the field itself; at the nodes
+    it is the grid value. Catches a wrong corner order of a tetrahedron, swapped barycentric
+    weights or a wrong cell."""
+    box, dims = ((0.0, -1.0, 0.5), (1.0, 1.0, 2.0)), (7, 6, 5)
+    lin = lambda r: 2.0 * r[:, 0] - 0.7 * r[:, 1] + 0.4 * r[:, 2] + 0.3
+    g = _field(lin, box, dims)
+    pts = np.random.default_rng(1).uniform(box[0], box[1], size=(500, 3))
+    np.testing.assert_allclose(oracle.tet_linear(g, box, dims, pts), lin(pts), rtol=0, atol=1e-12)
+    quad = lambda r: (r[:, 0] - 0.4) ** 2 + r[:, 1] * r[:, 2]
+    gq = _field(quad, box, dims)
+    nodes = oracle.grid_nodes(box, dims)[::7]
+    np.testing.assert_allclose(oracle.tet_linear(gq, box, dims, nodes), quad(nodes), atol=1e-12)
+
+
+def test_iso_surface_of_a_linear_field_is_the_plane():
+    """f = x: the surface is the plane x = t across the whole box, area = y-extent x
+    z-extent, every normal along -x (toward lower density). Catches a wrong crossing
+    weight, a missing quad half and a wrong orientation rule."""
+    box, dims = ((0.0, 0.0, 0.0), (1.0, 2.0, 1.0)), (6, 5, 4)
+    g = _field(lambda r: r[:, 0], box, dims)
+    t = 0.43
+    tris = oracle.iso_surface(g, box, dims, t)
+    assert tris.shape[0] > 0
+    np.testing.assert_allclose(tris[:, :, 0], t, atol=1e-12)
+    n = np.cross(tris[:, 1] - tris[:, 0], tris[:, 2] - tris[:, 0])
+    area = 0.5 * np.linalg.norm(n, axis=1)
+    assert area.sum() == pytest.approx(2.0, rel=1e-12)
+    assert np.all(n[:, 0] < 0) and np.allclose(n[:, 1:], 0.0, atol=1e-12)
+
+
+def test_iso_surface_of_a_ball_is_closed_and_encloses_its_volume():
+    """f = -|r - c|^2, t = -R^2: a closed surface (every edge shared by two triangles,
+    Euler characteristic 2) enclosing a little less than 4/3 pi R^3 (outward orientation
+    gives a positive divergence-theorem volume). Catches holes from inconsistent tetrahedra,
+    flipped triangles and a wrong 2-2 quad split."""
+    box, dims = ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0)), (21, 21, 21)
+    c, R = np.array([0.52, 0.47, 0.5]), 0.3
+    g = _field(lambda r: -np.sum((r - c) ** 2, axis=1), box, dims)
+    tris = oracle.iso_surface(g, box, dims, -R * R)
+    vol = oracle.mesh_volume(tris)
+    # the linear interpolant of a concave field lies below it: the volume comes out a
+    # little small (by about 3 s^2 / (8 R^2) x 3 = 3% at s = 1/20)
+    true = 4.0 / 3.0 * math.pi * R ** 3
+    assert 0.95 * true < vol < true
+    key = np.round(tris.reshape(-1, 3) * 1e9).astype(np.int64)
+    _, vid = np.unique(key, axis=0, return_inverse=True)
+    vid = vid.reshape(-1, 3)
+    edges = np.sort(np.concatenate([vid[:, [0, 1]], vid[:, [1, 2]], vid[:, [2, 0]]]), axis=1)
+    ue, cnt = np.unique(edges, axis=0, return_counts=True)
+    assert np.all(cnt == 2)
+    nv = int(vid.max()) + 1
+    assert nv - ue.shape[0] + vid.shape[0] == 2
+
+
+def test_points_in_the_selection_volume():
+    """Inside the ball by more than two node spacings: selected; outside by as much: not."""
+    box, dims = ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0)), (21, 21, 21)
+    c, R = np.array([0.5, 0.5, 0.5]), 0.3
+    g = _field(lambda r: -np.sum((r - c) ** 2, axis=1), box, dims)
+    pts = np.random.default_rng(2).uniform(0, 1, size=(3000, 3))
+    f = oracle.tet_linear(g, box, dims, pts)
+    d = np.linalg.norm(pts - c, axis=1)
+    s = 1.0 / 20
+    assert np.all(f[d < R - 2 * s] > -R * R) and np.all(f[d > R + 2 * s] <= -R * R)
