@@ -82,8 +82,10 @@ enum { SF_SCOPE_CLIP = 0, SF_SCOPE_GLOBAL = 1 };
 enum { SF_PREC_FP32 = 0, SF_PREC_TF32 = 1, SF_PREC_3XTF32 = 2, SF_PREC_BF16 = 3 };
 
 /* Point densities: DIRECT evaluates the kernel sum at each point (self term
- * included); INTERP interpolates the ROI grid trilinearly (Sec. 3.1, last step). */
-enum { SF_POINTS_DIRECT = 0, SF_POINTS_INTERP = 1 };
+ * included); INTERP interpolates the ROI grid trilinearly (Sec. 3.1, last step);
+ * TETLIN takes the selection volume's piecewise-linear field (sf_iso_surface),
+ * so that sf_select with the surface's threshold picks the points inside it. */
+enum { SF_POINTS_DIRECT = 0, SF_POINTS_INTERP = 1, SF_POINTS_TETLIN = 2 };
 
 typedef struct {
     double lo[3];
@@ -253,6 +255,31 @@ int64_t sf_last_call_workspace(void);
 sf_status sf_select(sf_index *idx, const float *d_density, const uint32_t *d_ids, int64_t n,
                     int64_t n_total, double threshold, double percentile, uint8_t *d_mask,
                     uint32_t *d_sel_ids, int64_t *h_nsel, double *h_threshold, void *stream);
+
+/*
+ * sf_iso_surface -- the boundary of the selection volume (Sec. 4.1: a density
+ * threshold, an iso-surface of the density field computed on the GPU, the points
+ * inside it), as a triangle soup in device memory.
+ *
+ * d_grid: device float [dims[2]][dims[1]][dims[0]] over the closed box roi (as
+ * sf_kde_grid writes it). Every cell is split into the six tetrahedra around its
+ * main diagonal (for each ordering a, b, c of the axes: corners 0, e_a,
+ * e_a + e_b, (1,1,1), orderings (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y),
+ * (z,y,x)); the grid values are interpolated linearly on each, and the volume is
+ * where that field exceeds `threshold`. Its boundary: one triangle for a
+ * tetrahedron with one corner on the other side from the three others, two for
+ * two and two; corners are "inside" when value > threshold (compared in FP64);
+ * the crossing on an edge from corner a to b is P_a + (t - f_a)/(f_b - f_a)
+ * (P_b - P_a) in FP64; every triangle is oriented with its normal pointing away
+ * from the inside corners (toward lower density). Output d_tris: device float
+ * [capacity][9] (three vertices x, y, z), in cell order (x fastest), then
+ * tetrahedron order, then the case's triangles. *h_ntri (host, required) gets the
+ * number of triangles; more than capacity gives CAPACITY and writes nothing
+ * (d_tris may be NULL with capacity 0 to count). Synchronises the stream.
+ * Errors: INVALID_ARG, OOM, CUDA, CAPACITY.
+ */
+sf_status sf_iso_surface(const float *d_grid, const sf_box *roi, const int32_t dims[3], double threshold,
+                         float *d_tris, int64_t capacity, int64_t *h_ntri, void *stream);
 
 /*
  * sf_resample_grid -- a finished grid read at the nodes of another grid by

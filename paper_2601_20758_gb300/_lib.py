@@ -41,6 +41,7 @@ SF_PREC_3XTF32 = 2
 SF_PREC_BF16 = 3
 SF_POINTS_DIRECT = 0
 SF_POINTS_INTERP = 1
+SF_POINTS_TETLIN = 2
 SF_WS_GRID = 1
 SF_WS_POINTS = 2
 
@@ -107,6 +108,8 @@ _PROTOS = {
     "sf_query_workspace": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
                                           ctypes.POINTER(sf_params), _i32, ctypes.POINTER(_i64), _vp]),
     "sf_last_call_workspace": (_i64, []),
+    "sf_iso_surface": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), ctypes.c_double,
+                                      _vp, _i64, ctypes.POINTER(_i64), _vp]),
     "sf_resample_grid": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32),
                                         ctypes.POINTER(sf_box), ctypes.POINTER(_i32), ctypes.c_float,
                                         _i32, _vp, ctypes.POINTER(_i64), _vp]),
@@ -287,6 +290,19 @@ def sf_grid_work_counts(idx, roi: sf_box, dims, kernel, params, stream=None) -> 
                                                              ctypes.byref(params), c, _stream(stream)))
     keys = ("pairs", "leaf_visits", "staged", "full_tile", "evaluated")
     return {k: int(v) for k, v in zip(keys, c)}
+
+
+def sf_iso_surface(d_grid, roi: sf_box, dims, threshold, d_tris=None, stream=None) -> int:
+    """Triangles of the selection volume's boundary into d_tris (float32 [capacity, 9], or
+    None to count only); returns the triangle count."""
+    dd = _dims3(dims)
+    pg = _dev_buf(d_grid, "d_grid", "f32", max(dd[0], 0) * max(dd[1], 0) * max(dd[2], 0))
+    cap = 0 if d_tris is None else d_tris.numel() // 9
+    pt = None if d_tris is None else _dev_buf(d_tris, "d_tris", "f32", 9 * cap)
+    n = _i64(0)
+    _check("sf_iso_surface", load().sf_iso_surface(pg, ctypes.byref(roi), (_i32 * 3)(*dd), float(threshold),
+                                                   pt, cap, ctypes.byref(n), _stream(stream)))
+    return int(n.value)
 
 
 def sf_resample_grid(d_src, src_box: sf_box, src_dims, dst_box: sf_box, dst_dims, d_dst,

@@ -31,7 +31,7 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
                       float *d_pilot, cudaStream_t s);
 sf_status interp_points(sf_index *idx, const sf_box &roi, const GridSpec &g, const float *d_grid,
                         const int *d_leaves, int64_t nslots, float *d_rho_sorted, uint8_t *d_inroi,
-                        cudaStream_t s);
+                        cudaStream_t s, int tet);
 
 // Count the points of the scope and set N_eff (device); EMPTY_ROI is recorded
 // in the status word when the clip scope holds no point.
@@ -106,7 +106,8 @@ static sf_status check_params(const sf_index *idx, const sf_params *p, int kerne
     if (p->prec != SF_PREC_FP32 && p->prec != SF_PREC_TF32 && p->prec != SF_PREC_3XTF32 &&
         p->prec != SF_PREC_BF16)
         return fail(SF_ERR_INVALID_ARG, "%s: unsupported precision %d", fn, p->prec);
-    if (p->points_mode != SF_POINTS_DIRECT && p->points_mode != SF_POINTS_INTERP)
+    if (p->points_mode != SF_POINTS_DIRECT && p->points_mode != SF_POINTS_INTERP &&
+        p->points_mode != SF_POINTS_TETLIN)
         return fail(SF_ERR_INVALID_ARG, "%s: unknown points_mode %d", fn, p->points_mode);
     if (p->reserved != 0) return fail(SF_ERR_INVALID_ARG, "%s: reserved must be 0", fn);
     switch (p->rule) {
@@ -304,7 +305,8 @@ sf_status sf_kde_points(sf_index *idx, const sf_box *roi, const int32_t *dims, i
         (params->rule != SF_BW_KNN || params->points_mode != SF_POINTS_DIRECT))
         return fail(SF_ERR_INVALID_ARG, "sf_kde_points: TF32 / 3xTF32 / BF16 need rule KNN and DIRECT");
     GridSpec g;
-    const bool need_grid = params->rule == SF_BW_MBE || params->points_mode == SF_POINTS_INTERP;
+    const bool interp = params->points_mode != SF_POINTS_DIRECT;
+    const bool need_grid = params->rule == SF_BW_MBE || interp;
     if (need_grid) SF_TRY(make_grid(*roi, dims, g, "sf_kde_points"));
     cudaStream_t s = (cudaStream_t)stream;
     *h_count = 0;
@@ -323,12 +325,13 @@ sf_status sf_kde_points(sf_index *idx, const sf_box *roi, const int32_t *dims, i
     SF_TRY_SCRATCH(sc);
     if (params->prec != SF_PREC_FP32) {
         SF_TRY(density_points_tc(idx, *roi, pr.call, params->prec, leaves, nleaf, rho, inroi, s));
-    } else if (params->points_mode == SF_POINTS_INTERP) {
+    } else if (interp) {
         Scratch gs(s);
         float *grid = gs.get<float>((int64_t)g.nx * g.ny * g.nz);
         SF_TRY_SCRATCH(gs);
         SF_TRY(density_grid(idx, *roi, g, pr.call, grid, nullptr, s));
-        SF_TRY(interp_points(idx, *roi, g, grid, leaves, nleaf, rho, inroi, s));
+        SF_TRY(interp_points(idx, *roi, g, grid, leaves, nleaf, rho, inroi, s,
+                             params->points_mode == SF_POINTS_TETLIN));
     } else {
         SF_TRY(density_points(idx, *roi, pr.call, leaves, nleaf, rho, inroi, s));
     }
@@ -349,7 +352,7 @@ sf_status sf_query_workspace(sf_index *idx, const sf_box *roi, const int32_t *di
         return fail(SF_ERR_INVALID_ARG,
                     "sf_query_workspace: rule MBE's workspace depends on its adaptive lengths (kNN and fixed rules only)");
     GridSpec g;
-    const bool need_grid = what == SF_WS_GRID || params->points_mode == SF_POINTS_INTERP;
+    const bool need_grid = what == SF_WS_GRID || params->points_mode != SF_POINTS_DIRECT;
     if (need_grid) SF_TRY(make_grid(*roi, dims, g, "sf_query_workspace"));
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc(s);
@@ -362,7 +365,7 @@ sf_status sf_query_workspace(sf_index *idx, const sf_box *roi, const int32_t *di
         SF_TRY(grid_workspace(idx, *roi, g, pr.call, &b, s));
         b += base + scratch_round(sizeof(double));  // the mass word (h_mass given)
     } else {
-        const bool interp = params->points_mode == SF_POINTS_INTERP && params->prec == SF_PREC_FP32;
+        const bool interp = params->points_mode != SF_POINTS_DIRECT && params->prec == SF_PREC_FP32;
         SF_TRY(points_workspace(idx, *roi, interp ? &g : nullptr, pr.call, base, &b, s));
     }
     *h_bytes = b;

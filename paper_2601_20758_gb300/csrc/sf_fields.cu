@@ -127,3 +127,176 @@ extern "C" sf_status sf_resample_grid(const float *d_src, const sf_box *src_box,
     }
     return SF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Selection volume boundary (sf_iso_surface)
+// ---------------------------------------------------------------------------
+namespace sf {
+
+namespace {
+
+struct IsoGrid {
+    int n[3];
+    double lo[3], s[3];
+    double t;
+};
+
+// Corner c (0..3) of the tetrahedron of ordering o (0..5), as 0/1 offsets in a bitmask
+// x | y << 1 | z << 2: corners 0, e_a, e_a + e_b, (1,1,1) for the orderings
+// (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x).
+__device__ __forceinline__ int tet_corner(int o, int c) {
+    const int a = o >> 1;                                            // first axis: 0,0,1,1,2,2
+    const int b = (o == 0 || o == 5) ? 1 : ((o == 1 || o == 3) ? 2 : 0);  // second axis
+    if (c == 0) return 0;
+    if (c == 1) return 1 << a;
+    if (c == 2) return (1 << a) | (1 << b);
+    return 7;
+}
+
+// Triangles of one tetrahedron: 0, 1 or 2 (count only when out == nullptr).
+__device__ int tet_triangles(const IsoGrid &G, const float *__restrict__ grid, int cx, int cy, int cz,
+                             int o, float *out) {
+    double P[4][3], f[4];
+    bool in[4];
+    int nin = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int m = tet_corner(o, c);
+        const int ix = cx + (m & 1), iy = cy + ((m >> 1) & 1), iz = cz + (m >> 2);
+        f[c] = (double)grid[((int64_t)iz * G.n[1] + iy) * G.n[0] + ix];
+        P[c][0] = G.lo[0] + (double)ix * G.s[0];
+        P[c][1] = G.lo[1] + (double)iy * G.s[1];
+        P[c][2] = G.lo[2] + (double)iz * G.s[2];
+        in[c] = f[c] > G.t;
+        nin += in[c];
+    }
+    if (nin == 0 || nin == 4) return 0;
+    const int ntri = nin == 2 ? 2 : 1;
+    if (!out) return ntri;
+    auto cross = [&](int a, int b, double *r) {
+        const double w = (G.t - f[a]) / (f[b] - f[a]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] = P[a][k] + w * (P[b][k] - P[a][k]);
+    };
+    double cen[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (in[c])
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cen[k] += P[c][k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) cen[k] /= (double)nin;
+    double V[2][3][3];
+    if (ntri == 1) {
+        int lone = -1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (in[c] == (nin == 1)) lone = c;   // the corner on its own side
+        int j = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c != lone) cross(lone, c, V[0][j++]);
+    } else {
+        int I = -1, J = -1, K = -1, Lc = -1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (in[c]) {
+                if (I < 0) I = c; else J = c;
+            } else {
+                if (K < 0) K = c; else Lc = c;
+            }
+        }
+        cross(I, K, V[0][0]);
+        cross(I, Lc, V[0][1]);
+        cross(J, Lc, V[0][2]);
+        cross(I, K, V[1][0]);
+        cross(J, Lc, V[1][1]);
+        cross(J, K, V[1][2]);
+    }
+    for (int q = 0; q < ntri; ++q) {
+        double *a = V[q][0], *b = V[q][1], *c = V[q][2];
+        const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                             e1[0] * e2[1] - e1[1] * e2[0]};
+        const double dn = n[0] * (a[0] - cen[0]) + n[1] * (a[1] - cen[1]) + n[2] * (a[2] - cen[2]);
+        const int ib = dn < 0.0 ? 2 : 1, ic = dn < 0.0 ? 1 : 2;   // toward the inside: flip
+        float *w = out + 9 * q;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            w[k] = (float)a[k];
+            w[3 + k] = (float)V[q][ib][k];
+            w[6 + k] = (float)V[q][ic][k];
+        }
+    }
+    return ntri;
+}
+
+// One thread per cell: its triangle count (pass 1) or its triangles at off[cell] (pass 2).
+template <bool EMIT>
+__global__ void k_iso(const float *__restrict__ grid, IsoGrid G, uint32_t *__restrict__ cnt,
+                      const uint32_t *__restrict__ off, float *__restrict__ tris) {
+    const int64_t nc = (int64_t)(G.n[0] - 1) * (G.n[1] - 1) * (G.n[2] - 1);
+    for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < nc;
+         cell += (int64_t)gridDim.x * blockDim.x) {
+        const int cx = (int)(cell % (G.n[0] - 1));
+        const int cy = (int)((cell / (G.n[0] - 1)) % (G.n[1] - 1));
+        const int cz = (int)(cell / ((int64_t)(G.n[0] - 1) * (G.n[1] - 1)));
+        if (!EMIT) {
+            uint32_t t = 0;
+            for (int o = 0; o < 6; ++o) t += (uint32_t)tet_triangles(G, grid, cx, cy, cz, o, nullptr);
+            cnt[cell] = t;
+        } else {
+            float *w = tris + 9 * (int64_t)off[cell];
+            for (int o = 0; o < 6; ++o) w += 9 * tet_triangles(G, grid, cx, cy, cz, o, w);
+        }
+    }
+}
+
+}  // namespace
+
+}  // namespace sf
+
+extern "C" sf_status sf_iso_surface(const float *d_grid, const sf_box *roi, const int32_t dims[3],
+                                    double threshold, float *d_tris, int64_t capacity, int64_t *h_ntri,
+                                    void *stream) {
+    clear_error();
+    if (!d_grid || !roi || !dims || !h_ntri) return fail(SF_ERR_INVALID_ARG, "sf_iso_surface: NULL argument");
+    if (!std::isfinite(threshold)) return fail(SF_ERR_INVALID_ARG, "sf_iso_surface: threshold must be finite");
+    if (capacity < 0 || (capacity > 0 && !d_tris))
+        return fail(SF_ERR_INVALID_ARG, "sf_iso_surface: bad capacity / output");
+    IsoGrid G;
+    for (int k = 0; k < 3; ++k) {
+        if (!std::isfinite(roi->lo[k]) || !std::isfinite(roi->hi[k]) || !(roi->hi[k] > roi->lo[k]))
+            return fail(SF_ERR_INVALID_ARG, "sf_iso_surface: roi axis %d must satisfy lo < hi", k);
+        if (dims[k] < 2 || dims[k] > 4096)
+            return fail(SF_ERR_INVALID_ARG, "sf_iso_surface: dims[%d] outside [2, 4096]", k);
+        G.n[k] = dims[k];
+        G.lo[k] = roi->lo[k];
+        G.s[k] = (roi->hi[k] - roi->lo[k]) / (double)(dims[k] - 1);
+    }
+    G.t = threshold;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nc = (int64_t)(G.n[0] - 1) * (G.n[1] - 1) * (G.n[2] - 1);
+    Scratch sc(s);
+    uint32_t *cnt = sc.get<uint32_t>(nc);
+    uint32_t *off = sc.get<uint32_t>(nc);
+    uint32_t *tot = sc.get<uint32_t>(1);
+    SF_TRY_SCRATCH(sc);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nc + 255) / 256, 152 * 16));
+    SF_TRY_CUDA(launch(k_iso<false>, dim3(blocks), dim3(256), 0, s, d_grid, G, cnt,
+                       (const uint32_t *)nullptr, (float *)nullptr));
+    SF_TRY(scan_u32(cnt, off, nc, tot, s));
+    uint32_t h = 0;
+    SF_TRY_CUDA(cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s));
+    SF_TRY_CUDA(cudaStreamSynchronize(s));
+    *h_ntri = h;
+    if ((int64_t)h > capacity) {
+        if (capacity == 0 && !d_tris) return SF_OK;   // counting only
+        return fail(SF_ERR_CAPACITY, "sf_iso_surface: %u triangles exceed capacity %lld", h, (long long)capacity);
+    }
+    if (h > 0)
+        SF_TRY_CUDA(launch(k_iso<true>, dim3(blocks), dim3(256), 0, s, d_grid, G, (uint32_t *)nullptr,
+                           (const uint32_t *)off, d_tris));
+    return SF_OK;
+}

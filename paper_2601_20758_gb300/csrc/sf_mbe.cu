@@ -61,6 +61,39 @@ __device__ __forceinline__ float trilinear(const float *__restrict__ grid, const
     return c0 * (1.f - t[2]) + c1 * t[2];
 }
 
+// The piecewise-linear field of the selection volume at (x, y, z): the cell as for
+// trilinear, the tetrahedron of the axis ordering with u_a >= u_b >= u_c (ties by
+// the lower axis first) around the cell's main diagonal, and
+// f = f0 + u_a (f1 - f0) + u_b (f2 - f1) + u_c (f3 - f2) along its corners
+// 0, e_a, e_a + e_b, (1, 1, 1). FP64 throughout, one rounding at the end.
+__device__ __forceinline__ float tet_linear(const float *__restrict__ grid, const InterpGrid &g,
+                                            float x, float y, float z) {
+    const double v[3] = {((double)x - g.lo[0]) * g.inv_s[0], ((double)y - g.lo[1]) * g.inv_s[1],
+                         ((double)z - g.lo[2]) * g.inv_s[2]};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    int c[3];
+    double u[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int ci = (int)floor(v[k]);
+        ci = min(max(ci, 0), n[k] - 2);
+        c[k] = ci;
+        u[k] = v[k] - (double)ci;
+    }
+    // the axis order, descending u, ties to the lower axis
+    int a = 0, b = 1, d = 2;
+    if (u[b] > u[a]) { const int t = a; a = b; b = t; }
+    if (u[d] > u[b]) { const int t = b; b = d; d = t; }
+    if (u[b] > u[a]) { const int t = a; a = b; b = t; }
+    const int64_t st[3] = {1, g.nx, (int64_t)g.nx * g.ny};
+    const float *base = grid + c[2] * st[2] + c[1] * st[1] + c[0];
+    const double f0 = base[0];
+    const double f1 = base[st[a]];
+    const double f2 = base[st[a] + st[b]];
+    const double f3 = base[st[0] + st[1] + st[2]];
+    return (float)(f0 + u[a] * (f1 - f0) + u[b] * (f2 - f1) + u[d] * (f3 - f2));
+}
+
 __global__ void k_box_flags(const float4 *__restrict__ pos, int64_t n, float3 lo, float3 hi,
                             uint32_t *__restrict__ flags) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -142,9 +175,10 @@ __global__ void k_asl(const uint32_t *__restrict__ list, int64_t m, const float 
 }
 
 // Slot i = t * 32 + l is the point of sorted index leaves[t] * 32 + l.
+// tet: the selection volume's piecewise-linear field instead of trilinear.
 __global__ void k_interp(const float4 *__restrict__ pos, int64_t n, const int *__restrict__ leaves,
                          int64_t nslots, float3 lo, float3 hi, const float *__restrict__ grid,
-                         InterpGrid g, float *__restrict__ rho, uint8_t *__restrict__ inroi) {
+                         InterpGrid g, int tet, float *__restrict__ rho, uint8_t *__restrict__ inroi) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslots * kLeaf;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = (int64_t)leaves[i / kLeaf] * kLeaf + (i % kLeaf);
@@ -153,7 +187,7 @@ __global__ void k_interp(const float4 *__restrict__ pos, int64_t n, const int *_
             const float4 p = pos[j];
             in = p.x >= lo.x && p.x <= hi.x && p.y >= lo.y && p.y <= hi.y && p.z >= lo.z &&
                  p.z <= hi.z;
-            if (in) rho[i] = trilinear(grid, g, p.x, p.y, p.z);
+            if (in) rho[i] = tet ? tet_linear(grid, g, p.x, p.y, p.z) : trilinear(grid, g, p.x, p.y, p.z);
         }
         inroi[i] = in ? 1 : 0;
     }
@@ -279,12 +313,12 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
 
 sf_status interp_points(sf_index *idx, const sf_box &roi, const GridSpec &g, const float *d_grid,
                         const int *d_leaves, int64_t nslots, float *d_rho_sorted, uint8_t *d_inroi,
-                        cudaStream_t s) {
+                        cudaStream_t s, int tet) {
     float3 lo, hi;
     box_bounds(roi, lo, hi);
     SF_TRY_CUDA(launch(k_interp, dim3(sgrid(nslots * kLeaf)), dim3(256), 0, s,
                        (const float4 *)idx->pos, idx->n, d_leaves, nslots, lo, hi, d_grid,
-                       interp_grid(g), d_rho_sorted, d_inroi));
+                       interp_grid(g), tet, d_rho_sorted, d_inroi));
     return SF_OK;
 }
 
