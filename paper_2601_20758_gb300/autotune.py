@@ -6,11 +6,14 @@ granularity at which dense tiles are split). For a given index and batch shape, 
 candidate is planned, warmed up and timed with CUDA events on the caller's
 stream; the fastest is cached in a JSON file keyed by the batch's signature
 (points, ROI count, total nodes, kernel, rule, scope), so later plans of the
-same shape reuse it without timing.
+same shape reuse it without timing. The key also holds the device (name and
+compute capability) and a digest of the built library, so a choice made on
+another GPU or by an earlier build of the kernels is timed again, not reused.
 """
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import json
 import os
 
@@ -25,9 +28,35 @@ def cache_path() -> str:
                                                   "tune.json"))
 
 
-def signature(n_points: int, dims_list, kernel: int, params) -> str:
+_LIB_DIGEST = {}
+
+
+def library_digest(path: str = None) -> str:
+    """First 12 hex digits of the SHA-256 of the built library file (cached per mtime)."""
+    path = L.LIB_PATH if path is None else path
+    st = os.stat(path)
+    key = (path, st.st_mtime_ns, st.st_size)
+    if key not in _LIB_DIGEST:
+        h = hashlib.sha256()
+        with open(path, "rb") as f:
+            for chunk in iter(lambda: f.read(1 << 20), b""):
+                h.update(chunk)
+        _LIB_DIGEST[key] = h.hexdigest()[:12]
+    return _LIB_DIGEST[key]
+
+
+def device_id(device=None) -> str:
+    """The CUDA device's name and compute capability, e.g. 'NVIDIA GB300-sm103'."""
+    import torch
+    d = torch.cuda.current_device() if device is None else device
+    major, minor = torch.cuda.get_device_capability(d)
+    return f"{torch.cuda.get_device_name(d)}-sm{major}{minor}"
+
+
+def signature(n_points: int, dims_list, kernel: int, params, device: str = "", build: str = "") -> str:
     nodes = sum(int(d[0]) * int(d[1]) * int(d[2]) for d in dims_list)
-    return f"n{n_points}-r{len(dims_list)}-g{nodes}-k{kernel}-b{params.rule}-s{params.scope}"
+    return (f"n{n_points}-r{len(dims_list)}-g{nodes}-k{kernel}-b{params.rule}-s{params.scope}"
+            f"-p{getattr(params, 'prec', 0)}|{device}|{build}")
 
 
 def _load_cache():
@@ -60,7 +89,7 @@ def tune_batch(idx, boxes, dims_list, kernel, params, outs, stream=None, reps: i
     """Return (tile_z, items_per_slot, timings_ms) for this batch shape."""
     import torch
     n = L.sf_index_size(idx)
-    key = signature(n, dims_list, kernel, params)
+    key = signature(n, dims_list, kernel, params, device_id(), library_digest())
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
