@@ -87,6 +87,25 @@ enum { SF_PREC_FP32 = 0, SF_PREC_TF32 = 1, SF_PREC_3XTF32 = 2, SF_PREC_BF16 = 3 
  * so that sf_select with the surface's threshold picks the points inside it. */
 enum { SF_POINTS_DIRECT = 0, SF_POINTS_INTERP = 1, SF_POINTS_TETLIN = 2 };
 
+/* Exact moment acceleration of grids (sf_kde_grid; Eq. 4 is a polynomial in
+ * the offsets inside its support). With the Epanechnikov kernel and one
+ * smoothing length for every particle (rule FIXED, and the pilot density of
+ * rule MBE, Eq. 2), the sum over the points of an index node that lies wholly
+ * inside the support of a grid node r is
+ *     c (M0 - sum_k (M0 (r_k - mu_k)^2 + C_k) / l_k^2)
+ * from the node's point count M0, centroid mu and central second moments C_k,
+ * so only the nodes that straddle the support's edge are summed point by
+ * point. The result is the same sum as the pair-by-pair gather up to rounding
+ * (FP32 terms, FP64 accumulation). The pair-by-pair gather is faster whenever
+ * it can run (the straddling shell holds most of the pairs unless l is many
+ * leaf widths), but its per-tile candidate lists are bounded by 2^31 entries;
+ * the moment form keeps no lists. SF_ACCEL_AUTO (0, the default): the gather,
+ * and the moment form where the gather's lists would exceed that bound;
+ * SF_ACCEL_NONE: the gather only (CAPACITY past the bound); SF_ACCEL_MOMENTS:
+ * the moment form wherever it applies. The moments (48 bytes per index node,
+ * about 1.5 bytes per point) are built with the index. */
+enum { SF_ACCEL_AUTO = 0, SF_ACCEL_NONE = 1, SF_ACCEL_MOMENTS = 2 };
+
 typedef struct {
     double lo[3];
     double hi[3];
@@ -103,11 +122,11 @@ typedef struct {
     int32_t scope;       /* SF_SCOPE_*                                           */
     int32_t prec;        /* SF_PREC_* (non-FP32: sf_kde_points only)             */
     int32_t points_mode; /* SF_POINTS_*                                          */
-    int32_t reserved;    /* must be 0                                            */
+    int32_t accel;       /* SF_ACCEL_* (grids; 0 = AUTO)                         */
 } sf_params;
 
 /* Fill *p with the defaults: KNN, k = 32, cap 5, percentiles 20/80, natural
- * log, GLOBAL scope, FP32, DIRECT points. */
+ * log, GLOBAL scope, FP32, DIRECT points, ACCEL_AUTO. */
 void sf_params_default(sf_params *p);
 
 /*
@@ -117,8 +136,9 @@ void sf_params_default(sf_params *p);
  * by a GPU index: points radix-sorted by 63-bit Morton key (21 bits per axis
  * over the cloud's bounding box), stored as float4 (x, y, z, h) in that
  * order; leaves are runs of 32 consecutive sorted points and every upper
- * level groups 32 nodes; each node keeps its bounding box and the largest
- * smoothing length below it.
+ * level groups 32 nodes; each node keeps its bounding box, the largest
+ * smoothing length below it and the moments of its points (count, centroid,
+ * central second moments; see SF_ACCEL_AUTO).
  *
  * d_xyz : device float32 [n][3] (x, y, z interleaved); read only, not kept.
  * n     : 1 <= n < 2^31.
@@ -177,7 +197,8 @@ sf_status sf_knn_neighbours(sf_index *idx, int32_t k, uint32_t *d_nbr, float *d_
  * synchronises the stream.
  * Errors: INVALID_ARG, OOM, CUDA, DEGENERATE (MBE with N_B < 2 or P80 == P20),
  * EMPTY_ROI (scope CLIP and no point in B; d_out is zero-filled), CAPACITY (the
- * per-tile candidate lists would exceed 2^31 entries: fewer nodes or a smaller ROI).
+ * per-tile candidate lists would exceed 2^31 entries: fewer nodes or a smaller ROI;
+ * not where SF_ACCEL_AUTO hands the grid to the moment form).
  * The call synchronises the stream once to size its work lists (before the
  * density kernels run); EMPTY_ROI is returned by the call itself.
  */
@@ -352,6 +373,8 @@ sf_status sf_batch_kde_grid(sf_index *idx, int32_t nroi, const sf_box *rois, con
  * It computes the same grid as sf_kde_grid, with the same kernels and node
  * coordinates, for rules SF_BW_KNN and SF_BW_FIXED (both scopes); rule
  * SF_BW_MBE needs scratch proportional to the cloud and gives INVALID_ARG.
+ * It always sums pair by pair (params->accel may be AUTO or NONE; MOMENTS
+ * gives INVALID_ARG), and reports CAPACITY-free sizes only as stated below.
  * All scratch lives in one fixed array of about 0.55 MB in device memory,
  * which every GPU that loads the library holds until the process exits; it
  * limits dims[k] to at most 1024 and the grid to at most 65536 tiles of

@@ -42,6 +42,7 @@ SF_PREC_BF16 = 3
 SF_POINTS_DIRECT = 0
 SF_POINTS_INTERP = 1
 SF_POINTS_TETLIN = 2
+SF_ACCEL_AUTO, SF_ACCEL_NONE, SF_ACCEL_MOMENTS = 0, 1, 2
 SF_WS_GRID = 1
 SF_WS_POINTS = 2
 
@@ -60,7 +61,7 @@ class sf_params(ctypes.Structure):
                 ("p_lo", ctypes.c_double), ("p_hi", ctypes.c_double),
                 ("log_base", ctypes.c_double), ("scope", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("points_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("accel", ctypes.c_int32)]
 
 
 class sf_tune(ctypes.Structure):
@@ -197,14 +198,15 @@ def make_box(lo, hi) -> sf_box:
 
 
 def make_params(rule=SF_BW_KNN, k=32, fixed_h=(0.0, 0.0, 0.0), cap_factor=5.0, p_lo=20.0,
-                p_hi=80.0, log_base=0.0, scope=SF_SCOPE_GLOBAL, points_mode=SF_POINTS_DIRECT):
+                p_hi=80.0, log_base=0.0, scope=SF_SCOPE_GLOBAL, points_mode=SF_POINTS_DIRECT,
+                accel=0):
     p = sf_params()
     load().sf_params_default(ctypes.byref(p))
     p.rule, p.k = rule, k
     for i in range(3):
         p.fixed_h[i] = float(fixed_h[i])
     p.cap_factor, p.p_lo, p.p_hi, p.log_base = cap_factor, p_lo, p_hi, log_base
-    p.scope, p.points_mode = scope, points_mode
+    p.scope, p.points_mode, p.accel = scope, points_mode, accel
     return p
 
 
@@ -414,3 +416,11 @@ def sf_last_error() -> str:
 
 def sf_launch_count() -> int:
     return int(load().sf_launch_count())
+
+
+def sf_kernel_timing(name: str):
+    """(total ms, launches) recorded for the named kernel since the last reset
+    (recording is on between sf_kernel_timing_enable(1) and (0))."""
+    ms, n = _dbl(0.0), _i64(0)
+    _check("sf_kernel_timing", load().sf_kernel_timing(name.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)

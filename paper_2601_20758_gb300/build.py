@@ -14,6 +14,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libscalefree.so")
 
 SOURCES = ["sf_prims.cu", "sf_index.cu", "sf_density.cu", "sf_knn.cu", "sf_select.cu", "sf_roi.cu",
+           "sf_moments.cu",
            "sf_mbe.cu", "sf_api.cu", "sf_static.cu", "sf_fields.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",

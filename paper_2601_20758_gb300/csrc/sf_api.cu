@@ -109,7 +109,8 @@ static sf_status check_params(const sf_index *idx, const sf_params *p, int kerne
     if (p->points_mode != SF_POINTS_DIRECT && p->points_mode != SF_POINTS_INTERP &&
         p->points_mode != SF_POINTS_TETLIN)
         return fail(SF_ERR_INVALID_ARG, "%s: unknown points_mode %d", fn, p->points_mode);
-    if (p->reserved != 0) return fail(SF_ERR_INVALID_ARG, "%s: reserved must be 0", fn);
+    if (p->accel != SF_ACCEL_AUTO && p->accel != SF_ACCEL_NONE && p->accel != SF_ACCEL_MOMENTS)
+        return fail(SF_ERR_INVALID_ARG, "%s: bad accel %d", fn, p->accel);
     switch (p->rule) {
         case SF_BW_KNN:
             if (idx->bw_rule != SF_BW_KNN || idx->knn_k != p->k)
@@ -162,6 +163,7 @@ static sf_status prepare(sf_index *idx, const sf_box &roi, const GridSpec *g, in
     SF_TRY_SCRATCH(sc);
     SF_TRY_CUDA(cudaMemsetAsync(out.status, 0, sizeof(int), s));
     out.call.kernel = kernel;
+    out.call.accel = p.accel;
     out.call.dp = out.dp;
     out.call.ell = nullptr;
     out.call.nell_override = nullptr;
@@ -567,6 +569,7 @@ void sf_free_index(sf_index *idx) {
     cudaFree(idx->nhi);
     cudaFree(idx->nell);
     cudaFree(idx->d_status);
+    cudaFree(idx->mom);
     delete idx;
 }
 

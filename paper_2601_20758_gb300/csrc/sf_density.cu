@@ -46,18 +46,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Reciprocal of the hardware approximation (relative error below 2^-22). Used
-// for the conservative support filters and for u_k = s / l_k and c / prod l_k,
-// where a few ulps stay far inside the 1e-5 density tolerance.
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Squared-support slack of the filters (covers the reciprocal's error and the
-// rounding of the gap terms; the filters only ever admit too much).
-constexpr float kFilterSlack = 3.0e-5f;
 
 // Kernel-specific constants, in the units of q' used on the device:
 //   EPAN : q' = sum (d_k / l_k)^2,           support q' < 1,  weight c (1 - q')
@@ -122,17 +110,6 @@ __device__ __forceinline__ bool node_reaches(const EngineArgs &a, const float *u
     return q < KDef<KER>::rmul * KDef<KER>::rmul * (1.0f + kFilterSlack);
 }
 
-// The box [lo, hi] widened by a margin that covers the float rounding of box
-// and node coordinates (relative 1e-6 of the coordinates).
-__device__ __forceinline__ void widen_box(const float lo[3], const float hi[3], float wlo[3],
-                                          float whi[3]) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float m = 1.0e-6f * (fabsf(lo[k]) + fabsf(hi[k])) + 1.0e-30f;
-        wlo[k] = lo[k] - m;
-        whi[k] = hi[k] + m;
-    }
-}
 
 // Warp-cooperative resumable depth-first walk. Emits accepted leaf indices in
 // ascending order into out[0..), stopping once fewer than 32 slots remain.
@@ -185,7 +162,7 @@ __device__ int warp_walk_start(const TreeView &tv, const Test &test, int *stack,
 }
 
 // Exact float bounds of a closed double box: x >= lo_f <=> (double)x >= lo.
-static void float_bounds(const double lo[3], const double hi[3], float flo[3], float fhi[3]) {
+void float_bounds(const double lo[3], const double hi[3], float flo[3], float fhi[3]) {
     for (int k = 0; k < 3; ++k) {
         float a = (float)lo[k];
         if ((double)a < lo[k]) a = nextafterf(a, INFINITY);
@@ -1461,7 +1438,7 @@ static sf_status dispatch_once(int bw, bool clip, const MrArgs &a, int ips, Stat
     }
 }
 
-static float kernel_cnorm(int kernel) {
+float kernel_cnorm(int kernel) {
     const double pi = 3.14159265358979323846;
     if (kernel == SF_K_EPAN) return (float)(15.0 / (8.0 * pi));
     const double p3 = std::erf(3.0 / std::sqrt(2.0)) - std::sqrt(2.0 / pi) * 3.0 * std::exp(-4.5);
@@ -1480,7 +1457,7 @@ static EngineArgs engine_args(sf_index *idx, const sf_box &roi, const DensityCal
 }
 
 // Node coordinates r_k(i) = lo_k + i s_k in double, split into float (hi, lo).
-static void node_axes(const GridSpec &g, float2 *ax) {
+void node_axes(const GridSpec &g, float2 *ax) {
     const int nd[3] = {g.nx, g.ny, g.nz};
     size_t o = 0;
     for (int k = 0; k < 3; ++k)
@@ -1510,10 +1487,10 @@ static RoiDesc roi_desc(const GridSpec &g, int tz, const float2 *axis, int tile_
     return r;
 }
 
-static sf_status density_grid_impl(sf_index *idx, const sf_box &roi, const GridSpec &g,
-                                   const DensityCall &call, float *d_out, double *d_mass,
-                                   cudaStream_t s, unsigned long long *d_pairs, StatusPeek *peek,
-                                   int64_t *ws_bytes) {
+static sf_status density_grid_gather(sf_index *idx, const sf_box &roi, const GridSpec &g,
+                                     const DensityCall &call, float *d_out, double *d_mass,
+                                     cudaStream_t s, unsigned long long *d_pairs, StatusPeek *peek,
+                                     int64_t *ws_bytes) {
     constexpr int TZ = kTileZ;
     std::vector<float2> ax((size_t)g.nx + g.ny + g.nz);
     node_axes(g, ax.data());
@@ -1556,6 +1533,25 @@ static sf_status density_grid_impl(sf_index *idx, const sf_box &roi, const GridS
                            tiles, cell, d_mass));
     }
     return SF_OK;
+}
+
+// The pair-by-pair gather, or the exact moment form (sf_moments.cu) when the
+// call asks for it, or, under SF_ACCEL_AUTO, when the gather's candidate lists
+// would pass 2^31 entries (the gather stops at its sizing step, before any
+// density kernel has run). The pair count always takes the gather.
+static sf_status density_grid_impl(sf_index *idx, const sf_box &roi, const GridSpec &g,
+                                   const DensityCall &call, float *d_out, double *d_mass,
+                                   cudaStream_t s, unsigned long long *d_pairs, StatusPeek *peek,
+                                   int64_t *ws_bytes) {
+    if (!d_pairs && moments_apply(call)) {
+        if (call.accel == SF_ACCEL_MOMENTS)
+            return density_grid_moments(idx, roi, g, call, d_out, d_mass, s, ws_bytes, peek);
+        const sf_status st = density_grid_gather(idx, roi, g, call, d_out, d_mass, s, nullptr, peek, ws_bytes);
+        if (st != SF_ERR_CAPACITY) return st;
+        clear_error();
+        return density_grid_moments(idx, roi, g, call, d_out, d_mass, s, ws_bytes, peek);
+    }
+    return density_grid_gather(idx, roi, g, call, d_out, d_mass, s, d_pairs, peek, ws_bytes);
 }
 
 sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,

@@ -274,7 +274,8 @@ extern "C" sf_status sf_build_index(const float *d_xyz, int64_t n, void *stream,
         (e = cudaMalloc(&idx->nlo, total * sizeof(float4))) != cudaSuccess ||
         (e = cudaMalloc(&idx->nhi, total * sizeof(float4))) != cudaSuccess ||
         (e = cudaMalloc(&idx->nell, total * sizeof(float4))) != cudaSuccess ||
-        (e = cudaMalloc(&idx->d_status, sizeof(int))) != cudaSuccess)
+        (e = cudaMalloc(&idx->d_status, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&idx->mom, 3 * total * sizeof(float4))) != cudaSuccess)
         return cleanup(fail(SF_ERR_OOM, "sf_build_index: cudaMalloc: %s", cudaGetErrorString(e)));
     if ((e = cudaMemsetAsync(idx->d_status, 0, sizeof(int), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(idx->nell, 0, total * sizeof(float4), s)) != cudaSuccess)
@@ -298,6 +299,7 @@ extern "C" sf_status sf_build_index(const float *d_xyz, int64_t n, void *stream,
             SF_TRY_CUDA(launch(k_inner_boxes, dim3(blocks_for(idx->cnt[l] * 32, 256)), dim3(256), 0, s,
                                idx->nlo, idx->nhi, idx->off[l - 1], idx->cnt[l - 1], idx->off[l],
                                idx->cnt[l]));
+        SF_TRY(build_moments(idx, s));
         int hb[6];
         SF_TRY_CUDA(cudaMemcpyAsync(hb, bb, sizeof hb, cudaMemcpyDeviceToHost, s));
         SF_TRY_CUDA(cudaStreamSynchronize(s));

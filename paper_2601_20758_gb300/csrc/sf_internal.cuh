@@ -177,6 +177,7 @@ struct sf_index {
     int knn_k = 0;
     float fixed_h[3] = {0, 0, 0};
     int *d_status = nullptr;  // device status word
+    float4 *mom = nullptr;    // per node: (mu_hi, M0), (mu_lo, -), (C, -); see build_moments
     std::mutex mu;
 
     sf::TreeView view() const {
@@ -225,6 +226,31 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
 }
 __device__ __forceinline__ f32x2 f2_ld(const float *p) {  // 8-byte aligned
     return *reinterpret_cast<const f32x2 *>(p);
+}
+
+// Reciprocal of the hardware approximation (relative error below 2^-22). Used
+// for the conservative support filters and for u_k = s / l_k and c / prod l_k,
+// where a few ulps stay far inside the 1e-5 density tolerance.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Squared-support slack of the filters (covers the reciprocal's error and the
+// rounding of the gap terms; the filters only ever admit too much).
+constexpr float kFilterSlack = 3.0e-5f;
+
+// The box [lo, hi] widened by a margin that covers the float rounding of box
+// and node coordinates (relative 1e-6 of the coordinates).
+__device__ __forceinline__ void widen_box(const float lo[3], const float hi[3], float wlo[3],
+                                          float whi[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float m = 1.0e-6f * (fabsf(lo[k]) + fabsf(hi[k])) + 1.0e-30f;
+        wlo[k] = lo[k] - m;
+        whi[k] = hi[k] + m;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -293,6 +319,13 @@ __global__ void k_set_params(DensityParams *dp, const unsigned long long *cnt, i
 sf_status set_density_params(sf_index *idx, bool clip, const sf_box &roi, const float ell[3],
                              DensityParams *d_dp, int *d_status, cudaStream_t s);
 
+// Exact float bounds of a closed double box: x >= lo_f <=> (double)x >= lo.
+void float_bounds(const double lo[3], const double hi[3], float flo[3], float fhi[3]);
+// Normalisation constant of the kernel: 15/(8 pi) or 1/((2 pi)^1.5 P3).
+float kernel_cnorm(int kernel);
+// Node coordinates r_k(i) = lo_k + i s_k in double, split into float (hi, lo), x then y then z.
+void node_axes(const GridSpec &g, float2 *ax);
+
 struct DensityCall {
     int kernel;       // SF_K_*
     int bw;           // BwMode
@@ -301,7 +334,25 @@ struct DensityCall {
     const DensityParams *dp;  // device
     float4 *nell_override;     // node max-ell array to use (null: the index's own)
     int prec = SF_PREC_FP32;   // grids: SF_PREC_* (non-FP32: Gaussian with kNN or fixed lengths)
+    int accel = SF_ACCEL_AUTO; // grids: SF_ACCEL_* (the moment form: Epanechnikov, uniform lengths)
 };
+
+// Per-node moments of the index (sf_moments.cu), built once with the index:
+// for node g, mom[3g] = (mu_hi, M0), mom[3g+1] = (mu_lo, 0), mom[3g+2] = (C, 0)
+// with M0 the point count, mu = centroid (mu_hi + mu_lo in float pairs) and
+// C_k = sum (y_k - mu_k)^2 (FP64 sums, rounded once).
+sf_status build_moments(sf_index *idx, cudaStream_t s);
+// Grid density by exact moments (Epanechnikov, BW_UNIFORM only); same contract
+// as density_grid. ws_bytes (nullable): return the call's bytes instead of running.
+sf_status density_grid_moments(sf_index *idx, const sf_box &roi, const GridSpec &g,
+                               const DensityCall &call, float *d_out, double *d_mass,
+                               cudaStream_t s, int64_t *ws_bytes, StatusPeek *peek);
+// Sum of n per-tile (or per-block) FP64 partial masses times cell, into *out.
+__global__ void k_mass_final(const double *__restrict__ part, int64_t n, double cell, double *out);
+// True when the moment form applies to this call (Epanechnikov, one length per axis).
+inline bool moments_apply(const DensityCall &c) {
+    return c.kernel == SF_K_EPAN && c.bw == BW_UNIFORM && c.accel != SF_ACCEL_NONE;
+}
 
 // peek (nullable): a status word read back at the call's sizing synchronisation.
 sf_status density_grid(sf_index *idx, const sf_box &roi, const GridSpec &g,

@@ -290,6 +290,7 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
     pc.ell = nullptr;
     pc.dp = d_dp;
     pc.nell_override = nullptr;
+    pc.accel = p.accel;  // Epanechnikov: the pilot's one length makes it a moment sum
     SF_TRY(density_grid(idx, roi, g, pc, pilot, nullptr, s));
     // 4. pilot at the particles, aveDen, adaptive lengths
     const InterpGrid ig = interp_grid(g);

@@ -115,8 +115,8 @@ extern "C" sf_status sf_kde_grid_static(sf_index *idx, const sf_box *roi, const 
     if (kernel != SF_K_EPAN && kernel != SF_K_GAUSS3)
         return fail(SF_ERR_INVALID_ARG, "sf_kde_grid_static: unknown kernel %d", kernel);
     if ((p->scope != SF_SCOPE_CLIP && p->scope != SF_SCOPE_GLOBAL) || p->prec != SF_PREC_FP32 ||
-        p->reserved != 0)
-        return fail(SF_ERR_INVALID_ARG, "sf_kde_grid_static: bad scope, precision or reserved field");
+        (p->accel != SF_ACCEL_AUTO && p->accel != SF_ACCEL_NONE))
+        return fail(SF_ERR_INVALID_ARG, "sf_kde_grid_static: bad scope, precision or accel field");
     float ell[3] = {0.f, 0.f, 0.f};
     int bw;
     if (p->rule == SF_BW_KNN) {

@@ -14,6 +14,8 @@ times (one sf_kde_grid per ROI on one index):
 - grids: per-call and batched grids of two zoom ROIs agree, and a recompute is
   bit-identical.
 """
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -146,3 +148,55 @@ def test_large_cloud_sampled_densities_against_oracle(large):
         assert part["pairs"].max() > 0, label
         density_check(gv, part, label=label)
         o += m
+
+
+def test_large_full_cube_by_moments_when_lists_overflow(large):
+    """Rule FIXED, Epanechnikov, clip scope, the full-cube ROI at 256^3 with
+    lengths of 0.06 per axis (the scale of the estimator's pilot lengths, Eq. 1,
+    at this size): the gather's candidate lists would pass 2^31 entries, so the
+    default (SF_ACCEL_AUTO) computes the grid by exact moments, one k_mom_grid
+    launch; 48 sampled nodes (half uniform, half nearest to seeded points)
+    against the oracle's sum over all 1,073,741,824 points, taken in chunks of
+    2^24 points (the sum's terms are the same; only the FP64 order differs)."""
+    L, idx, p, xyz, rois = large
+    box = rois[0]
+    h = (0.06, 0.06, 0.06)
+    pf = L.make_params(rule=L.SF_BW_FIXED, fixed_h=h, scope=L.SF_SCOPE_CLIP)
+    G = DIMS[0] * DIMS[1] * DIMS[2]
+    grid = torch.empty(G, device="cuda")
+    lib = L.load()
+    lib.sf_kernel_timing_enable(1)
+    lib.sf_kernel_timing_reset()
+    try:
+        L.sf_kde_grid(idx, L.make_box(*box), DIMS, L.SF_K_EPAN, pf, grid)
+        torch.cuda.synchronize()
+        ms, launches = L.sf_kernel_timing("k_mom_grid")
+    finally:
+        lib.sf_kernel_timing_enable(0)
+    assert launches == 1, launches
+    print(f"full cube 1.07B 256^3 by moments: {ms:.0f} ms")
+    g = grid.cpu().numpy()
+    del grid
+    rng = np.random.default_rng(606)
+    pts = xyz[np.sort(rng.choice(N, 24, replace=False))].astype(np.float64)
+    flat = np.unique(np.concatenate([rng.choice(G, 24, replace=False), _nearest_nodes(box, DIMS, pts)]))
+    (ax, ay, az), _ = oracle.grid_axes(box, DIMS)
+    nodes = np.stack([ax[flat % DIMS[0]], ay[(flat // DIMS[0]) % DIMS[1]],
+                      az[flat // (DIMS[0] * DIMS[1])]], axis=1)
+    chunk = 1 << 24
+    starts = range(0, N, chunk)
+    nb = sum(int(oracle.in_box(xyz[a:a + chunk], box).sum()) for a in starts)
+    ell = np.broadcast_to(np.array([float(np.float32(v)) for v in h]), (chunk, 3))
+
+    workers = max(1, oracle.num_threads())
+
+    def part(a):  # the oracle's sum over one chunk, one thread per chunk (no GIL held in C)
+        oracle.set_num_threads(1)
+        sl = xyz[a:a + chunk]
+        return oracle.density_at(sl, ell, nodes, oracle.EPAN, 1.0 / nb, member=oracle.in_box(sl, box))
+
+    with ThreadPoolExecutor(workers) as ex:
+        parts = list(ex.map(part, starts))
+    ref = {k: sum(pp[k] for pp in parts) for k in parts[0]}
+    assert ref["pairs"].min() > 0
+    density_check(g[flat], ref, label="full cube by moments")
