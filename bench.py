@@ -92,6 +92,8 @@ def parse():
                     help="skip the batched-vs-plain comparison over 64 uneven ROIs")
     ap.add_argument("--no-prec", action="store_true",
                     help="skip the tensor-core precision variants of the point densities")
+    ap.add_argument("--no-mbe", action="store_true",
+                    help="skip the paper's estimator (MBE, Epanechnikov) per ROI")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-slots", type=int, default=4, help="concurrent requests (streams)")
@@ -491,6 +493,8 @@ def run_large(ctx):
         e2e = None if args.no_e2e else run_e2e_large(ctx, idx, boxes, p, grids, sum(pairs))
         baselines = None if args.no_baselines else run_baselines(ctx, idx, p, rois, grids, roi_ms)
         serving = None if args.no_serve else run_serving(ctx, idx, n, p, rois)
+        mbe = None if args.no_mbe else run_mbe(ctx, idx, rois, LARGE_DIMS, grids[0],
+                                               (("auto", L.SF_ACCEL_AUTO), ("moments", L.SF_ACCEL_MOMENTS)))
     finally:
         L.sf_free_index(idx)
         torch.cuda.empty_cache()
@@ -522,8 +526,47 @@ def run_large(ctx):
             "k_grid_work_ms_per_roi": per_roi_work,
             "setup": setup, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "serving": serving,
-            "precomputed_fields": baselines,
+            "precomputed_fields": baselines, "mbe": mbe,
             "cosmology_16M": nested}
+
+
+def run_mbe(ctx, idx, rois, dims, out, forms):
+    """The paper's own estimator per ROI (Epanechnikov, clip scope; Eqs. 1, 2, 5,
+    6, 7: percentile lengths, pilot grid, pilot at the particles, adaptive
+    lengths, final grid), one call per ROI and form, CUDA events on the stream.
+    Forms: the default (the pilot by the gather while its candidate lists fit,
+    else by exact moments) and the moment form forced. Whole-cube ROIs run once
+    (seconds each); smaller ones after one untimed call."""
+    L, torch, stream = ctx["L"], ctx["torch"], ctx["stream"]
+    lib = L.load()
+    rows = []
+    for lo, hi in rois:
+        box = L.make_box(lo, hi)
+        edge = float(hi[0] - lo[0])
+        row = {"edge": edge}
+        for name, accel in forms:
+            if edge >= 1.0 and accel == L.SF_ACCEL_MOMENTS:
+                continue  # the default already takes the moment form there
+            p = L.make_params(rule=L.SF_BW_MBE, scope=L.SF_SCOPE_CLIP, accel=accel)
+            if edge < 1.0:
+                L.sf_kde_grid(idx, box, dims, L.SF_K_EPAN, p, out, stream=stream)
+            torch.cuda.synchronize()
+            lib.sf_kernel_timing_enable(1)
+            lib.sf_kernel_timing_reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            L.sf_kde_grid(idx, box, dims, L.SF_K_EPAN, p, out, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            mom_ms, mom_n = L.sf_kernel_timing("k_mom_grid")
+            work_ms, _ = L.sf_kernel_timing("k_grid_work")
+            lib.sf_kernel_timing_enable(0)
+            lib.sf_kernel_timing_reset()
+            row[name] = {"ms": a.elapsed_time(b), "pilot_by_moments": mom_n > 0,
+                         "k_mom_grid_ms": mom_ms, "k_grid_work_ms": work_ms}
+        rows.append(row)
+    return {"estimator": "MBE (Eqs. 1, 2, 5, 6, 7), Epanechnikov, clip scope, cap 5 spacings",
+            "grid": list(dims), "rois": rows}
 
 
 def run_baselines(ctx, idx, p, rois, grids, roi_ms):
@@ -732,6 +775,13 @@ def run_cosmology(ctx, nested):
         out["batched"] = run_batched(args, L, torch, d_xyz, p, stream)
     if not args.no_prec:
         out["precision"] = run_precision(L, torch, d_xyz, p, boxes[1], stream)
+    if not args.no_mbe:
+        idx = L.sf_build_index(d_xyz, stream)
+        try:
+            out["mbe"] = run_mbe(ctx, idx, rois, COSMO_DIMS, grids[0],
+                                 (("auto", L.SF_ACCEL_AUTO), ("moments", L.SF_ACCEL_MOMENTS)))
+        finally:
+            L.sf_free_index(idx)
     if not nested:
         out["e2e"] = None if args.no_e2e else run_e2e_cosmology(ctx, xyz, boxes, p, pairs_step)
         cpu = None

@@ -192,7 +192,12 @@ sf_status sf_knn_neighbours(sf_index *idx, int32_t k, uint32_t *d_nbr, float *d_
  * i_z*dims[0]*dims[1], as in Algorithms 2 and 4).
  * rule KNN needs sf_bandwidths(KNN) first; FIXED uses params->fixed_h; MBE
  * runs the paper's pilot -> adaptive-length -> final pipeline for this ROI
- * (Algorithm 1) with scope CLIP.
+ * (Algorithm 1) with scope CLIP. It finds B's particles through the index (the
+ * leaves whose box meets B), so its per-call scratch and time follow the ROI;
+ * its adaptive lengths live in two buffers the index allocates at its first
+ * MBE call and keeps until sf_free_index (16 bytes per point and per node).
+ * MBE calls on one index run one at a time (host lock; the device work of a
+ * call is ordered after the previous call's, on any stream).
  * h_mass (nullable, host): FP64 total mass sum_n rho_n s_x s_y s_z; giving it
  * synchronises the stream.
  * Errors: INVALID_ARG, OOM, CUDA, DEGENERATE (MBE with N_B < 2 or P80 == P20),
@@ -217,7 +222,7 @@ sf_status sf_kde_grid(sf_index *idx, const sf_box *roi, const int32_t dims[3], i
  * meets the box), so for the kNN and fixed rules the call's time and scratch
  * grow with the ROI's points, not with the cloud: about 24 bytes per ROI point
  * plus 9 bytes per point of the leaves that meet the box (sf_query_workspace
- * gives the exact figure). Rule MBE also needs 16 bytes per cloud point.
+ * gives the exact figure). Rule MBE keeps its resident buffers as for sf_kde_grid.
  * Scope CLIP with no point in B returns EMPTY_ROI with *h_count = 0.
  * DIRECT sums the kernels at each point (the point's own kernel included);
  * INTERP interpolates the grid of the same dims trilinearly.

@@ -15,8 +15,6 @@ sf_status scatter_bandwidths(const sf_index *idx, float *d_h_orig, cudaStream_t 
 sf_status select_points(const float *d_density, const uint32_t *d_ids, int64_t n, int64_t n_total,
                         double threshold, double percentile, uint8_t *d_mask, uint32_t *d_sel_ids,
                         int64_t *h_nsel, double *h_threshold, cudaStream_t s);
-sf_status roi_leaf_list(sf_index *idx, const sf_box &roi, Scratch &sc, int **d_list,
-                        int64_t *h_nleaf, StatusPeek *peek, cudaStream_t s);
 sf_status roi_compact(sf_index *idx, const int *d_leaves, int64_t nslots, const uint8_t *d_inroi,
                       const float *d_rho, float *d_density, uint32_t *d_ids, int64_t capacity,
                       int64_t *h_count, cudaStream_t s);
@@ -154,7 +152,36 @@ struct Prepared {
     int *status = nullptr;  // this call's device status word (ST_EMPTY in clip scope)
     float4 *ell = nullptr;
     float4 *nell = nullptr;
+    // rule MBE: the index's resident length buffers are this call's until it
+    // returns; the device work queued by then is marked for the next call
+    std::unique_lock<std::mutex> mbe_lock;
+    sf_index *idx = nullptr;
+    cudaStream_t stream = nullptr;
+    ~Prepared() {
+        if (mbe_lock.owns_lock() && idx->mbe_done) cudaEventRecord(idx->mbe_done, stream);
+    }
 };
+
+// The estimator's resident buffers (16 bytes per point and per node), made at
+// its first call on the index; later calls order their device work after the
+// previous call's, whatever stream either ran on.
+static sf_status mbe_buffers(sf_index *idx, cudaStream_t s) {
+    if (!idx->mbe_ell) {
+        cudaError_t e;
+        if ((e = cudaMalloc(&idx->mbe_ell, sizeof(float4) * idx->n)) != cudaSuccess ||
+            (e = cudaMalloc(&idx->mbe_nell, sizeof(float4) * idx->nnodes)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&idx->mbe_done, cudaEventDisableTiming)) != cudaSuccess) {
+            cudaFree(idx->mbe_ell);
+            cudaFree(idx->mbe_nell);
+            idx->mbe_ell = idx->mbe_nell = nullptr;
+            idx->mbe_done = nullptr;
+            return fail(SF_ERR_OOM, "rule MBE: resident length buffers: %s", cudaGetErrorString(e));
+        }
+        return SF_OK;
+    }
+    SF_TRY_CUDA(cudaStreamWaitEvent(s, idx->mbe_done, 0));
+    return SF_OK;
+}
 
 static sf_status prepare(sf_index *idx, const sf_box &roi, const GridSpec *g, int kernel,
                          const sf_params &p, Scratch &sc, Prepared &out, cudaStream_t s) {
@@ -169,9 +196,13 @@ static sf_status prepare(sf_index *idx, const sf_box &roi, const GridSpec *g, in
     out.call.nell_override = nullptr;
     if (p.rule == SF_BW_MBE) {
         if (!g) return fail(SF_ERR_INVALID_ARG, "rule MBE needs the grid dims");
-        out.ell = sc.get<float4>(idx->n);
-        out.nell = sc.get<float4>(idx->nnodes);
-        SF_TRY_SCRATCH(sc);
+        KTimer t("mbe_prepare", s);
+        out.mbe_lock = std::unique_lock<std::mutex>(idx->mbe_mu);
+        out.idx = idx;
+        out.stream = s;
+        SF_TRY(mbe_buffers(idx, s));
+        out.ell = idx->mbe_ell;
+        out.nell = idx->mbe_nell;
         SF_TRY(mbe_prepare(idx, roi, *g, kernel, p, out.dp, out.ell, out.nell, nullptr, s));
         out.call.bw = BW_ANISO;
         out.call.clip = 1;
@@ -570,6 +601,9 @@ void sf_free_index(sf_index *idx) {
     cudaFree(idx->nell);
     cudaFree(idx->d_status);
     cudaFree(idx->mom);
+    cudaFree(idx->mbe_ell);
+    cudaFree(idx->mbe_nell);
+    if (idx->mbe_done) cudaEventDestroy(idx->mbe_done);
     delete idx;
 }
 

@@ -161,10 +161,11 @@ __global__ void k_inner_boxes(float4 *__restrict__ nlo, float4 *__restrict__ nhi
 // ---------------------------------------------------------------------------
 __global__ void k_leaf_ell(const float4 *__restrict__ pos, const float4 *__restrict__ ell,
                            int64_t n, int64_t nleaf, int clip, double3 blo, double3 bhi,
-                           float4 *__restrict__ nell) {
+                           float4 *__restrict__ nell, const int *__restrict__ list) {
     const int lane = threadIdx.x & 31;
-    const int64_t leaf = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (leaf >= nleaf) return;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nleaf) return;
+    const int64_t leaf = list ? (int64_t)list[w] : w;
     const int64_t i = leaf * kLeaf + lane;
     float3 m = make_float3(0.f, 0.f, 0.f);
     float hmin = INFINITY;  // smallest positive length of the leaf (any axis)
@@ -215,16 +216,19 @@ __global__ void k_inner_ell(float4 *__restrict__ nell, int64_t child_off, int64_
 }
 
 sf_status build_node_ell(sf_index *idx, int bw, const float4 *ell, const sf_box *clip_roi,
-                         float4 *d_nell, cudaStream_t s) {
+                         float4 *d_nell, cudaStream_t s, const int *d_leaves, int64_t nleaf) {
     double3 blo = make_double3(0, 0, 0), bhi = make_double3(0, 0, 0);
     if (clip_roi) {
         blo = make_double3(clip_roi->lo[0], clip_roi->lo[1], clip_roi->lo[2]);
         bhi = make_double3(clip_roi->hi[0], clip_roi->hi[1], clip_roi->hi[2]);
     }
     const float4 *e = (bw == BW_ANISO) ? ell : nullptr;
-    SF_TRY_CUDA(launch(k_leaf_ell, dim3(blocks_for(idx->cnt[0] * 32, 256)), dim3(256), 0, s,
-                       (const float4 *)idx->pos, e, idx->n, idx->cnt[0], clip_roi ? 1 : 0, blo,
-                       bhi, d_nell));
+    const int64_t nl = d_leaves ? nleaf : idx->cnt[0];
+    if (d_leaves)  // leaves off the list hold no contributing point
+        SF_TRY_CUDA(cudaMemsetAsync(d_nell, 0, sizeof(float4) * idx->cnt[0], s));
+    SF_TRY_CUDA(launch(k_leaf_ell, dim3(blocks_for(nl * 32, 256)), dim3(256), 0, s,
+                       (const float4 *)idx->pos, e, idx->n, nl, clip_roi ? 1 : 0, blo,
+                       bhi, d_nell, d_leaves));
     for (int l = 1; l < idx->nlevels; ++l)
         SF_TRY_CUDA(launch(k_inner_ell, dim3(blocks_for(idx->cnt[l] * 32, 256)), dim3(256), 0, s,
                            d_nell, idx->off[l - 1], idx->cnt[l - 1], idx->off[l], idx->cnt[l]));

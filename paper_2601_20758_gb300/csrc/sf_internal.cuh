@@ -178,6 +178,12 @@ struct sf_index {
     float fixed_h[3] = {0, 0, 0};
     int *d_status = nullptr;  // device status word
     float4 *mom = nullptr;    // per node: (mu_hi, M0), (mu_lo, -), (C, -); see build_moments
+    // The estimator's per-point adaptive lengths and per-node maxima (rule MBE),
+    // allocated at its first call and kept; calls take mbe_mu for their whole
+    // duration and order their device work after the previous call's (mbe_done).
+    float4 *mbe_ell = nullptr, *mbe_nell = nullptr;
+    cudaEvent_t mbe_done = nullptr;
+    std::mutex mbe_mu;
     std::mutex mu;
 
     sf::TreeView view() const {
@@ -372,9 +378,16 @@ sf_status density_points_tc(sf_index *idx, const sf_box &roi, const DensityCall 
                             uint8_t *d_inroi, cudaStream_t s);
 
 // Node max smoothing length per axis for BW_ISO (from pos.w) or BW_ANISO (from ell,
-// only points inside roi when clip) into d_nell.
+// only points inside roi when clip) into d_nell. d_leaves (nullable): only these
+// nleaf leaves can hold a contributing point; every other leaf gets 0.
 sf_status build_node_ell(sf_index *idx, int bw, const float4 *ell, const sf_box *clip_roi,
-                         float4 *d_nell, cudaStream_t s);
+                         float4 *d_nell, cudaStream_t s, const int *d_leaves = nullptr,
+                         int64_t nleaf = 0);
+
+// Leaves whose bounding box meets the ROI: *d_list (in sc, ascending), *h_nleaf.
+// Synchronises the stream once (the count); peek (nullable) is read at that point.
+sf_status roi_leaf_list(sf_index *idx, const sf_box &roi, Scratch &sc, int **d_list,
+                        int64_t *h_nleaf, StatusPeek *peek, cudaStream_t s);
 
 // Batched grids over many ROIs (sf_density.cu).
 struct BatchPlan;

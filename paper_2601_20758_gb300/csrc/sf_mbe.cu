@@ -1,6 +1,8 @@
 // sf_mbe.cu -- the paper's modified Breiman estimator for one ROI (Sec. 3.1,
 // Algorithm 1), ahead of the final gather:
-//   1. the particles of the box B and their count N_B;
+//   1. the particles of the box B and their count N_B, found through the index
+//      (the points of the leaves whose bounding box meets B), so that this and
+//      every later step scale with the ROI's leaves, not with the cloud;
 //   2. per-axis percentiles P^(20), P^(80) of their coordinates (exact order
 //      statistics by radix selection) and l_k = 2 (P80 - P20) / log N_B (Eq. 1);
 //   3. pilot density at the grid nodes with the constant l (Eq. 2; Algorithm 2);
@@ -8,10 +10,12 @@
 //      aveDen in FP64 (Eq. 5; Algorithm 3's reduction, done as deterministic
 //      per-block FP64 partial sums), and l_k^(j) = min(l_k (aveDen/pDen)^(1/3),
 //      cap s_k) (Eq. 6), with pDen = 0 giving the cap;
-//   5. per-node maxima of l^(j) for the traversal of the final gather (Eq. 7).
+//   5. per-node maxima of l^(j) for the traversal of the final gather (Eq. 7),
+//      from the leaves that meet B (every other leaf gets 0).
 // Also: trilinear interpolation of a grid at the ROI points (density "at any
 // position", the last step of Sec. 3.1).
 #include <cmath>
+#include <memory>
 
 #include "sf_internal.cuh"
 
@@ -94,21 +98,30 @@ __device__ __forceinline__ float tet_linear(const float *__restrict__ grid, cons
     return (float)(f0 + u[a] * (f1 - f0) + u[b] * (f2 - f1) + u[d] * (f3 - f2));
 }
 
-__global__ void k_box_flags(const float4 *__restrict__ pos, int64_t n, float3 lo, float3 hi,
-                            uint32_t *__restrict__ flags) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 p = pos[i];
-        flags[i] = (p.x >= lo.x && p.x <= hi.x && p.y >= lo.y && p.y <= hi.y && p.z >= lo.z &&
-                    p.z <= hi.z) ? 1u : 0u;
+// Slot t of the listed leaves = point leaves[t / 32] * 32 + t % 32: flags[t] = 1
+// when that point exists and lies in the closed box [lo, hi] (float bounds).
+__global__ void k_box_flags(const float4 *__restrict__ pos, int64_t n, const int *__restrict__ leaves,
+                            int64_t nslots, float3 lo, float3 hi, uint32_t *__restrict__ flags) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nslots;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = (int64_t)leaves[t / kLeaf] * kLeaf + (t % kLeaf);
+        uint32_t f = 0u;
+        if (i < n) {
+            const float4 p = pos[i];
+            f = (p.x >= lo.x && p.x <= hi.x && p.y >= lo.y && p.y <= hi.y && p.z >= lo.z &&
+                 p.z <= hi.z) ? 1u : 0u;
+        }
+        flags[t] = f;
     }
 }
 
+// The members' sorted positions at their scan positions (ascending, as the
+// leaves are listed in ascending order).
 __global__ void k_box_list(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ pos_,
-                           int64_t n, uint32_t *__restrict__ list) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        if (flags[i]) list[pos_[i]] = (uint32_t)i;
+                           const int *__restrict__ leaves, int64_t nslots, uint32_t *__restrict__ list) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nslots;
+         t += (int64_t)gridDim.x * blockDim.x)
+        if (flags[t]) list[pos_[t]] = (uint32_t)((int64_t)leaves[t / kLeaf] * kLeaf + (t % kLeaf));
 }
 
 __global__ void k_axis_keys(const float4 *__restrict__ pos, const uint32_t *__restrict__ list,
@@ -218,13 +231,20 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
     float3 blo, bhi;
     box_bounds(roi, blo, bhi);
     Scratch sc(s);
-    uint32_t *flags = sc.get<uint32_t>(n);
-    uint32_t *posn = sc.get<uint32_t>(n);
+    // phase timers (recorded only while sf_kernel_timing_enable is on)
+    auto phase = std::make_unique<KTimer>("mbe_members", s);
+    // 1. members of B, through the index: the leaves whose box meets B, then their points
+    int *leaves = nullptr;
+    int64_t nleaf = 0;
+    SF_TRY(roi_leaf_list(idx, roi, sc, &leaves, &nleaf, nullptr, s));
+    const int64_t slots = nleaf * kLeaf;
+    uint32_t *flags = sc.get<uint32_t>(slots);
+    uint32_t *posn = sc.get<uint32_t>(slots);
     uint32_t *total = sc.get<uint32_t>(1);
     SF_TRY_SCRATCH(sc);
-    // 1. members of B
-    SF_TRY_CUDA(launch(k_box_flags, dim3(sgrid(n)), dim3(256), 0, s, (const float4 *)idx->pos, n, blo, bhi, flags));
-    SF_TRY(scan_u32(flags, posn, n, total, s));
+    SF_TRY_CUDA(launch(k_box_flags, dim3(sgrid(slots)), dim3(256), 0, s, (const float4 *)idx->pos, n,
+                       (const int *)leaves, slots, blo, bhi, flags));
+    SF_TRY(scan_u32(flags, posn, slots, total, s));
     uint32_t hnb = 0;
     SF_TRY_CUDA(cudaMemcpyAsync(&hnb, total, sizeof hnb, cudaMemcpyDeviceToHost, s));
     SF_TRY_CUDA(cudaStreamSynchronize(s));
@@ -235,8 +255,9 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
     int64_t *ranks = sc.get<int64_t>(12);
     uint32_t *sel = sc.get<uint32_t>(12);
     SF_TRY_SCRATCH(sc);
-    SF_TRY_CUDA(launch(k_box_list, dim3(sgrid(n)), dim3(256), 0, s, (const uint32_t *)flags,
-                       (const uint32_t *)posn, n, list));
+    SF_TRY_CUDA(launch(k_box_list, dim3(sgrid(slots)), dim3(256), 0, s, (const uint32_t *)flags,
+                       (const uint32_t *)posn, (const int *)leaves, slots, list));
+    phase = std::make_unique<KTimer>("mbe_lengths", s);
     // 2. percentiles: order statistics at floor(pos) and floor(pos) + 1
     const double q[2] = {p.p_lo, p.p_hi};
     int64_t hr[12];
@@ -276,6 +297,7 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
         if (!(ell0[axis] > 0.0))
             return fail(SF_ERR_DEGENERATE, "MBE: percentile spread is zero on axis %d", axis);
     }
+    phase = std::make_unique<KTimer>("mbe_pilot", s);
     // 3. pilot density with the constant l (Eq. 2), clip scope
     const int64_t G = (int64_t)g.nx * g.ny * g.nz;
     float *pilot = d_pilot_out ? d_pilot_out : sc.get<float>(G);
@@ -292,6 +314,7 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
     pc.nell_override = nullptr;
     pc.accel = p.accel;  // Epanechnikov: the pilot's one length makes it a moment sum
     SF_TRY(density_grid(idx, roi, g, pc, pilot, nullptr, s));
+    phase = std::make_unique<KTimer>("mbe_asl", s);
     // 4. pilot at the particles, aveDen, adaptive lengths
     const InterpGrid ig = interp_grid(g);
     const unsigned gb = sgrid(nb);
@@ -308,7 +331,8 @@ sf_status mbe_prepare(sf_index *idx, const sf_box &roi, const GridSpec &g, int k
     SF_TRY_CUDA(launch(k_asl, dim3(gb), dim3(256), 0, s, (const uint32_t *)list, nb,
                        (const float *)pden, (const double *)ave, l0, cap, d_ell));
     // 5. node maxima over the members
-    SF_TRY(build_node_ell(idx, BW_ANISO, d_ell, &roi, d_nell, s));
+    phase = std::make_unique<KTimer>("mbe_node_ell", s);
+    SF_TRY(build_node_ell(idx, BW_ANISO, d_ell, &roi, d_nell, s, leaves, nleaf));
     return SF_OK;
 }
 

@@ -231,3 +231,47 @@ def test_mbe_16m_both_forms(L):
         np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6 * float(np.abs(b).max()))
     finally:
         L.sf_free_index(idx)
+
+
+def test_mbe_calls_on_two_streams_and_threads(L):
+    """The estimator's adaptive lengths live in buffers of the index: two host
+    threads running MBE grids of different ROIs on two streams at once get the
+    same grids as the same calls made one after the other, and match the oracle."""
+    import threading
+    xyz = synth.plain_cloud(6000, seed=77)
+    d = torch.from_numpy(xyz).cuda()
+    idx = L.sf_build_index(d)
+    try:
+        rois = [((0.05, 0.1, 0.0), (0.95, 0.9, 1.0)), ((0.2, 0.15, 0.25), (0.8, 0.7, 0.9))]
+        dims = [(26, 24, 22), (21, 19, 23)]
+        p = L.make_params(rule=L.SF_BW_MBE, scope=L.SF_SCOPE_CLIP)
+        seq = []
+        for r, dm in zip(rois, dims):
+            o = torch.empty(dm[0] * dm[1] * dm[2], device="cuda")
+            L.sf_kde_grid(idx, L.make_box(*r), dm, L.SF_K_EPAN, p, o)
+            seq.append(o.cpu().numpy())
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        outs = [torch.empty(dm[0] * dm[1] * dm[2], device="cuda") for dm in dims]
+        errs = []
+
+        def run(i):
+            try:
+                for _ in range(3):
+                    L.sf_kde_grid(idx, L.make_box(*rois[i]), dims[i], L.SF_K_EPAN, p, outs[i],
+                                  stream=streams[i])
+            except Exception as e:  # reported below
+                errs.append(e)
+
+        th = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        torch.cuda.synchronize()
+        assert not errs, errs
+        for i in range(2):
+            assert np.array_equal(outs[i].cpu().numpy(), seq[i]), i
+            ref = oracle.mbe(xyz, rois[i], dims[i], kernel=oracle.EPAN)
+            density_check(seq[i], ref["final"], rel=1e-5, label=f"mbe roi {i}")
+    finally:
+        L.sf_free_index(idx)
