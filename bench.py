@@ -645,14 +645,14 @@ def run_serving(ctx, idx, n, p, rois):
     free, _ = torch.cuda.mem_get_info()
     slots = args.serve_slots
 
-    def replay(cache):
-        reqs = serve.navigation_requests(args.serve_requests, rate=args.serve_rate, centre=centre,
-                                         seed=2601, bf16_share=0.3)
+    def replay(cache, supersede=False, rate=None, n_req=None):
+        reqs = serve.navigation_requests(n_req or args.serve_requests, rate=rate or args.serve_rate,
+                                         centre=centre, seed=2601, bf16_share=0.3)
         ex = serve.GpuExecutor(idx, p, L.SF_K_GAUSS3, n, slots=slots, max_nodes=256 ** 3, max_points=1,
                                cache=cache)
-        srv = serve.Server(ex, slots=slots, mem_budget=int(0.4 * free))
+        srv = serve.Server(ex, slots=slots, mem_budget=int(0.4 * free), supersede=supersede)
         try:
-            warm = [serve.Request(-1 - i, r.lo, r.hi, r.dims, want_points=False, prec=r.prec)
+            warm = [serve.Request(-1 - i, r.lo, r.hi, r.dims, want_points=False, prec=r.prec, client=1 + i)
                     for i, r in enumerate(reqs[:2 * slots])]
             srv.replay(warm)
             srv.completed.clear()
@@ -674,11 +674,17 @@ def run_serving(ctx, idx, n, p, rois):
 
     st = replay(None)
     st["with_view_cache"] = replay(serve.ViewCache(margin=0.25, coarsen_tol=0.3, max_nodes=384 ** 3))
+    # the recompute trigger: a newer view supersedes the waiting ones (one navigating client)
+    st["latest_view_wins"] = replay(None, supersede=True)
+    # every request computed, at lower arrival rates
+    st["rate_sweep"] = {f"{r:g}": replay(None, rate=r, n_req=200) for r in (25.0, 50.0)}
     st["rate_per_s"] = args.serve_rate
     st["stream"] = ("Poisson arrivals over the 1.07B-point cloud, zoom walk over log10 edge in "
                     "[-3, 0] (sigma 0.1 decade), pan <= half an edge, grid edge in "
                     "{64, 96, 128, 192, 256}^3; every request recomputes the ROI grid; 30% of the "
-                    "requests in BF16 (tensor-core grid variant), 70% FP32")
+                    "requests in BF16 (tensor-core grid variant), 70% FP32; latest_view_wins: "
+                    "waiting requests superseded by a newer view of the same client are dropped; "
+                    "rate_sweep: 200 requests at lower mean rates, all computed")
     return st
 
 

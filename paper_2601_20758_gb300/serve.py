@@ -36,6 +36,7 @@ class Request:
     select_pct: float = 90.0
     want_points: bool = True
     prec: str = "fp32"            # "fp32", or "bf16": tensor-core cross term for the point densities
+    client: int = 0               # the navigating view this request belongs to
     # filled by the server
     admitted: float = math.nan
     done: float = math.nan
@@ -56,12 +57,19 @@ def percentile(values, q):
 
 
 class Server:
-    """Continuous admission over `slots` fixed workers and a device-memory budget."""
+    """Continuous admission over `slots` fixed workers and a device-memory budget.
 
-    def __init__(self, executor, slots: int = 4, mem_budget: int = 1 << 34):
+    supersede (the recompute trigger of progressive navigation): a request that
+    arrives for a client drops that client's requests still waiting in the
+    queue -- their views are no longer on screen -- and they complete with
+    status "superseded" without being computed. Requests already running finish.
+    """
+
+    def __init__(self, executor, slots: int = 4, mem_budget: int = 1 << 34, supersede: bool = False):
         self.ex = executor
         self.slots = slots
         self.budget = mem_budget
+        self.supersede = bool(supersede)
         self._lock = threading.Condition()
         self._queue = collections.deque()
         self._free_slots = list(range(slots))
@@ -101,6 +109,16 @@ class Server:
                 self._lock.notify_all()
                 return
             req._need = need
+            if self.supersede:
+                keep = collections.deque()
+                for r in self._queue:
+                    if r.client == req.client:
+                        r.status = "superseded"
+                        r.done = self.now()
+                        self.completed.append(r)
+                    else:
+                        keep.append(r)
+                self._queue = keep
             self._queue.append(req)
             self._lock.notify_all()
 
@@ -183,6 +201,7 @@ class Server:
         svc = [1e3 * (r.done - r.admitted) for r in ok]
         return {"requests": len(self.completed), "done": len(ok),
                 "rejected": sum(r.status == "rejected" for r in self.completed),
+                "superseded": sum(r.status == "superseded" for r in self.completed),
                 "errors": sum(r.status.startswith("error") for r in self.completed),
                 "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
                 "service_p50_ms": percentile(svc, 50), "service_p99_ms": percentile(svc, 99),

@@ -130,3 +130,34 @@ def test_bf16_share_is_seeded_and_leaves_the_walk_alone():
     assert [(r.lo, r.dims, r.arrival) for r in a] == [(r.lo, r.dims, r.arrival) for r in b]
     share = sum(r.prec == "bf16" for r in b) / len(b)
     assert 0.24 < share < 0.36 and all(r.prec == "fp32" for r in a)
+
+
+def test_supersede_drops_waiting_views_of_the_same_client_only():
+    """Recompute trigger: with one slot busy, requests of client 0 arriving while
+    it runs replace each other in the queue (only the newest is computed); a
+    request of client 1 waiting at the same time is kept."""
+    ex = FakeExecutor(0.05)
+    srv = serve.Server(ex, slots=1, mem_budget=1 << 40, supersede=True)
+    try:
+        reqs = [serve.Request(rid=i, lo=(0, 0, 0), hi=(1, 1, 1), dims=(8, 8, 8), arrival=0.002 * i,
+                              client=0) for i in range(6)]
+        reqs.append(serve.Request(rid=100, lo=(0, 0, 0), hi=(1, 1, 1), dims=(8, 8, 8), arrival=0.003,
+                                  client=1))
+        st = srv.replay(reqs)
+    finally:
+        srv.close()
+    by = {r.rid: r.status for r in srv.completed}
+    assert by[0] == "done"                      # admitted at once
+    assert by[5] == "done" and by[100] == "done"
+    assert all(by[i] == "superseded" for i in range(1, 5))
+    assert st["superseded"] == 4 and st["done"] == 3
+    assert ex.order == [0, 100, 5] or ex.order == [0, 5, 100]
+    # without the trigger every request is computed, in arrival order
+    ex2 = FakeExecutor(0.01)
+    srv2 = serve.Server(ex2, slots=1, mem_budget=1 << 40)
+    try:
+        st2 = srv2.replay([serve.Request(rid=i, lo=(0, 0, 0), hi=(1, 1, 1), dims=(8, 8, 8),
+                                         arrival=0.001 * i) for i in range(5)])
+    finally:
+        srv2.close()
+    assert st2["done"] == 5 and st2["superseded"] == 0 and ex2.order == list(range(5))
