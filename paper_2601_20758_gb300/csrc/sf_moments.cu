@@ -61,7 +61,17 @@ __device__ __forceinline__ void store_moments(float4 *mom, int64_t g, double m, 
     mom[3 * g + 2] = make_float4((float)c[0], (float)c[1], (float)c[2], 0.f);
 }
 
-// One warp per leaf: count, centroid and central second moments in FP64 (two passes).
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One warp per leaf: count, centroid and central second moments, two passes over
+// the offsets e = y - y0 from the leaf's first point (FP32: the offsets are as
+// small as the leaf, so their sums keep about 24 bits relative to the leaf's
+// size); the centroid y0 + mean(e) is formed in FP64 once, by lane 0. FP64
+// stays out of the shuffles: its rate on this GPU is a small fraction of FP32's.
 __global__ void k_mom_leaf(const float4 *__restrict__ pos, int64_t n, int64_t nleaf,
                            float4 *__restrict__ mom) {
     const int lane = threadIdx.x & 31;
@@ -69,23 +79,29 @@ __global__ void k_mom_leaf(const float4 *__restrict__ pos, int64_t n, int64_t nl
     if (leaf >= nleaf) return;
     const int64_t i = leaf * kLeaf + lane;
     const bool v = i < n;
-    double y[3] = {0.0, 0.0, 0.0};
+    const float4 p0 = pos[leaf * kLeaf];
+    float e[3] = {0.f, 0.f, 0.f};
     if (v) {
         const float4 p = pos[i];
-        y[0] = p.x;
-        y[1] = p.y;
-        y[2] = p.z;
+        e[0] = p.x - p0.x;
+        e[1] = p.y - p0.y;
+        e[2] = p.z - p0.z;
     }
-    const double m = (double)__popc(__ballot_sync(0xffffffffu, v));
-    double mu[3], c[3];
+    const int m = __popc(__ballot_sync(0xffffffffu, v));
+    float eb[3], c[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) mu[k] = warp_sum_d(y[k]) / m;
+    for (int k = 0; k < 3; ++k) eb[k] = warp_sum_f(e[k]) / (float)m;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double e = v ? y[k] - mu[k] : 0.0;
-        c[k] = warp_sum_d(e * e);
+        const float d = v ? e[k] - eb[k] : 0.f;
+        c[k] = warp_sum_f(d * d);
     }
-    if (lane == 0) store_moments(mom, leaf, m, mu, c);
+    if (lane == 0) {
+        const double mu[3] = {(double)p0.x + (double)eb[0], (double)p0.y + (double)eb[1],
+                              (double)p0.z + (double)eb[2]};
+        const double cd[3] = {c[0], c[1], c[2]};
+        store_moments(mom, leaf, (double)m, mu, cd);
+    }
 }
 
 // One warp per inner node, one lane per child: M = sum M_c, mu = sum M_c mu_c / M,
