@@ -163,7 +163,10 @@ int64_t sf_index_size(const sf_index *idx);
  * SF_BW_FIXED: stores fixed_h (isotropic only if the three are equal).
  * SF_BW_MBE  : nothing to precompute (the rule is per ROI); returns SF_OK.
  * The result stays resident in the index and is used by later calls with the
- * same rule.
+ * same rule. The kernels are queued on `stream` and the call returns without
+ * waiting for them: a later call on another stream must be ordered after them
+ * (an event, or a synchronisation) -- streams created non-blocking do not wait
+ * for the legacy default stream.
  */
 sf_status sf_bandwidths(sf_index *idx, const sf_params *params, void *stream);
 

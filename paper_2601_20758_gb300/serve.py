@@ -256,7 +256,9 @@ class ViewCache:
 
 
 class GpuExecutor:
-    """Runs a request through the C ABI on the slot's own CUDA stream. Output
+    """Runs a request through the C ABI on the slot's own CUDA stream (the slot
+    streams are ordered after the caller's current stream at construction, so an
+    index and bandwidths built there just before are complete). Output
     buffers are preallocated per slot (max_nodes grid nodes, max_points ROI points);
     admission sizes each request by the library's own workspace figure. With a
     ViewCache, grid-only requests go through it (cache buffers: slots + 1, so a
@@ -274,6 +276,11 @@ class GpuExecutor:
         self.copy_back = copy_back
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.query_stream = torch.cuda.Stream()
+        # the slot streams do not wait for the legacy stream by themselves: order them
+        # after the work the caller queued on its current stream (the index, the bandwidths)
+        cur = torch.cuda.current_stream()
+        for st in self.streams + [self.query_stream]:
+            st.wait_stream(cur)
         self._qlock = threading.Lock()
         cap = n_points if max_points is None else int(max_points)
         dev = "cuda"
