@@ -5,8 +5,9 @@ new scale triggers a density recompute) turns into a stream of recompute
 requests. The server keeps the index and the bandwidths resident on the GPU;
 requests wait in arrival order and are admitted as soon as a slot is free and
 the device memory the request's calls will allocate (asked of the library
-with sf_query_workspace when the request arrives) fits the budget next to the
-requests already running. Each slot is a fixed worker thread with its own
+with sf_query_workspace when the request reaches the head of the queue, so
+that arrivals never wait on the GPU) fits the budget next to the requests
+already running. Each slot is a fixed worker thread with its own
 CUDA stream and preallocated output buffers, so admitted requests overlap on
 the device. Latency = completion time - arrival time on the host clock.
 
@@ -92,50 +93,64 @@ class Server:
         return time.perf_counter() - self._t0
 
     def submit(self, req: Request):
-        try:
-            need = int(self.ex.workspace(req))
-        except Exception as e:  # noqa: BLE001  (an invalid request fails alone)
-            with self._lock:
-                req.status = f"error: {e}"
-                req.done = self.now()
-                self.completed.append(req)
-                self._lock.notify_all()
-            return
+        """Queue a request (never blocks on the GPU: its workspace is asked of the
+        library when it reaches the head of the queue)."""
         with self._lock:
-            if need > self.budget:
-                req.status = "rejected"      # can never fit, even alone
-                req.done = self.now()
-                self.completed.append(req)
-                self._lock.notify_all()
-                return
-            req._need = need
+            req._need = None
             if self.supersede:
                 keep = collections.deque()
                 for r in self._queue:
                     if r.client == req.client:
-                        r.status = "superseded"
-                        r.done = self.now()
-                        self.completed.append(r)
+                        self._finish(r, "superseded")
                     else:
                         keep.append(r)
                 self._queue = keep
             self._queue.append(req)
             self._lock.notify_all()
 
-    def _admissible(self) -> bool:
-        return bool(self._queue and self._free_slots
-                    and self._in_flight + self._queue[0]._need <= self.budget)
+    def _finish(self, req: Request, status: str):
+        """Complete a request that will not run (lock held)."""
+        req.status = status
+        req.done = self.now()
+        self.completed.append(req)
+        self._lock.notify_all()
 
     def _dispatch(self):
         while True:
             with self._lock:
-                while not self._closed and not self._admissible():
+                while not self._closed and not (self._queue and self._free_slots):
                     self._lock.wait()
                 if self._closed and not self._queue:
                     for q in self._inbox:
                         q.put(None)
                     return
-                if not self._admissible():
+                if not (self._queue and self._free_slots):
+                    continue
+                head = self._queue[0]
+                need = head._need
+            if need is None:  # the library's figure for the head, outside the lock
+                try:
+                    need = int(self.ex.workspace(head))
+                except Exception as e:  # noqa: BLE001  (an invalid request fails alone)
+                    need = e
+            with self._lock:
+                if not self._queue or self._queue[0] is not head:
+                    continue           # superseded while its workspace was asked for
+                if isinstance(need, Exception):
+                    self._queue.popleft()
+                    self._finish(head, f"error: {need}")
+                    continue
+                head._need = need
+                if need > self.budget:
+                    self._queue.popleft()
+                    self._finish(head, "rejected")   # can never fit, even alone
+                    continue
+                while (self._in_flight + need > self.budget and not self._closed
+                       and self._queue and self._queue[0] is head):
+                    self._lock.wait()
+                if not self._queue or self._queue[0] is not head or not self._free_slots:
+                    continue
+                if self._in_flight + need > self.budget:
                     continue
                 req = self._queue.popleft()           # first come, first admitted
                 slot = self._free_slots.pop()
