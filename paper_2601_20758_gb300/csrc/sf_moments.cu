@@ -42,6 +42,15 @@ namespace sf {
 // --------------------------------------------------------------------------
 // Moments of the index nodes
 // --------------------------------------------------------------------------
+// s = a + b rounded, e = the exact error (a + b = s + e; Knuth's two-sum, no
+// ordering of |a| and |b| needed).
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -70,8 +79,9 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // One warp per leaf: count, centroid and central second moments, two passes over
 // the offsets e = y - y0 from the leaf's first point (FP32: the offsets are as
 // small as the leaf, so their sums keep about 24 bits relative to the leaf's
-// size); the centroid y0 + mean(e) is formed in FP64 once, by lane 0. FP64
-// stays out of the shuffles: its rate on this GPU is a small fraction of FP32's.
+// size); the centroid y0 + mean(e) is kept as the exact float pair of a two-sum.
+// No FP64: its rate on this GPU is a small fraction of FP32's, and even one
+// lane's FP64 instructions hold the pipe for a whole warp's worth of cycles.
 __global__ void k_mom_leaf(const float4 *__restrict__ pos, int64_t n, int64_t nleaf,
                            float4 *__restrict__ mom) {
     const int lane = threadIdx.x & 31;
@@ -96,11 +106,14 @@ __global__ void k_mom_leaf(const float4 *__restrict__ pos, int64_t n, int64_t nl
         const float d = v ? e[k] - eb[k] : 0.f;
         c[k] = warp_sum_f(d * d);
     }
-    if (lane == 0) {
-        const double mu[3] = {(double)p0.x + (double)eb[0], (double)p0.y + (double)eb[1],
-                              (double)p0.z + (double)eb[2]};
-        const double cd[3] = {c[0], c[1], c[2]};
-        store_moments(mom, leaf, (double)m, mu, cd);
+    if (lane == 0) {  // centroid p0 + mean(e) as an exact (hi, lo) float pair: no FP64
+        const float y0[3] = {p0.x, p0.y, p0.z};
+        float h[3], l[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) h[k] = two_sum(y0[k], eb[k], l[k]);
+        mom[3 * leaf + 0] = make_float4(h[0], h[1], h[2], (float)m);
+        mom[3 * leaf + 1] = make_float4(l[0], l[1], l[2], 0.f);
+        mom[3 * leaf + 2] = make_float4(c[0], c[1], c[2], 0.f);
     }
 }
 
@@ -162,15 +175,6 @@ constexpr int kMomLeaves = 64;      // straddling leaves gathered before they ar
 // 1 - kFullSlack: every pair it stands for is then inside the support by a
 // margin far beyond the rounding of q (and of the oracle's own test).
 constexpr float kFullSlack = 1.0e-4f;
-
-// s = a + b rounded, e = the exact error (a + b = s + e; Knuth's two-sum, no
-// ordering of |a| and |b| needed).
-__device__ __forceinline__ float two_sum(float a, float b, float &e) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return s;
-}
 
 struct MomArgs {
     TreeView tv;
