@@ -145,6 +145,10 @@ void sf_params_default(sf_params *p);
  * out   : receives the new index; free it with sf_free_index.
  * Synchronises `stream` (the node count is read back). Errors: INVALID_ARG,
  * OOM, CUDA.
+ * The calls' scratch comes from the device's default stream-ordered memory
+ * pool (cudaMallocAsync); the first index build sets that pool to keep the
+ * memory it has mapped between calls instead of returning it at every
+ * synchronisation (a setting of this process only).
  */
 sf_status sf_build_index(const float *d_xyz, int64_t n, void *stream, sf_index **out);
 
@@ -448,7 +452,8 @@ sf_status sf_kernel_timing_list(const char *name, double *h_ms, int64_t cap, int
  * CUDA errors of work still queued on the stream. */
 sf_status sf_sync_status(sf_index *idx, void *stream);
 
-/* Release the index and all of its device memory. Safe on NULL. */
+/* Release the index and all of its device memory, and hand the default pool's
+ * unused memory back to the system. Safe on NULL. */
 void sf_free_index(sf_index *idx);
 
 /* Message describing the last error of the calling thread ("" if none). */

@@ -604,7 +604,9 @@ void sf_free_index(sf_index *idx) {
     cudaFree(idx->mbe_ell);
     cudaFree(idx->mbe_nell);
     if (idx->mbe_done) cudaEventDestroy(idx->mbe_done);
+    const int dev = idx->device;
     delete idx;
+    trim_pool_memory(dev);
 }
 
 const char *sf_last_error(void) { return last_error_cstr(); }

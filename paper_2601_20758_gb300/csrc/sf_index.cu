@@ -215,6 +215,24 @@ __global__ void k_inner_ell(float4 *__restrict__ nell, int64_t child_off, int64_
     if (lane == 0) nell[off + node] = make_float4(m.x, m.y, m.z, 0.0f);
 }
 
+// The calls' scratch comes from the device's stream-ordered pool; by default the
+// pool returns freed memory to the system at every synchronisation, so each
+// call would map its scratch afresh. From the first index build on, the pool
+// keeps the memory it has mapped (the attribute lives with this process);
+// sf_free_index hands the pool's unused memory back.
+void keep_pool_memory(int device) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) != cudaSuccess) return;
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+}
+
+void trim_pool_memory(int device) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) != cudaSuccess) return;
+    cudaMemPoolTrimTo(pool, 0);
+}
+
 sf_status build_node_ell(sf_index *idx, int bw, const float4 *ell, const sf_box *clip_roi,
                          float4 *d_nell, cudaStream_t s, const int *d_leaves, int64_t nleaf) {
     double3 blo = make_double3(0, 0, 0), bhi = make_double3(0, 0, 0);
@@ -249,6 +267,7 @@ extern "C" sf_status sf_build_index(const float *d_xyz, int64_t n, void *stream,
     sf_index *idx = new sf_index();
     idx->n = n;
     cudaGetDevice(&idx->device);
+    keep_pool_memory(idx->device);
 
     // level sizes are a function of n alone
     int64_t c = (n + kLeaf - 1) / kLeaf, total = 0;

@@ -384,6 +384,10 @@ sf_status build_node_ell(sf_index *idx, int bw, const float4 *ell, const sf_box 
                          float4 *d_nell, cudaStream_t s, const int *d_leaves = nullptr,
                          int64_t nleaf = 0);
 
+// The device's stream-ordered pool keeps freed scratch while indexes exist / is trimmed.
+void keep_pool_memory(int device);
+void trim_pool_memory(int device);
+
 // Leaves whose bounding box meets the ROI: *d_list (in sc, ascending), *h_nleaf.
 // Synchronises the stream once (the count); peek (nullable) is read at that point.
 sf_status roi_leaf_list(sf_index *idx, const sf_box &roi, Scratch &sc, int **d_list,
