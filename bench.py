@@ -763,6 +763,19 @@ def run_cosmology(ctx, nested):
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] is not None else None
     roof["traffic"] = load_traffic(dom)
     roof["avg_launch_ms"] = avg_ms
+    if dom == "k_knn" and not args.no_count:
+        # the kNN is issue- and latency-bound: its rate of candidate distance evaluations
+        # (8 FP32 flops each: 3 differences, a product and two FMAs) against the FP32 rate
+        idx = L.sf_build_index(d_xyz, stream)
+        try:
+            wc = L.sf_knn_work_counts(idx, K_NN, stream)
+        finally:
+            L.sf_free_index(idx)
+        ach = wc["evaluations"] * 8 / (avg_ms * 1e-3) / 1e12
+        roof["issue"] = {"unit": "TFLOP/s", "work_unit": "8 FP32 flops per (query, candidate) distance",
+                         "evaluations_per_launch": wc["evaluations"],
+                         "candidates_per_query_leaf": wc["staged"] / max(wc["query_leaves"], 1),
+                         "achieved": ach, "peak": pk["fp32_tflops"], "frac": ach / pk["fp32_tflops"]}
     flat = sorted(x for r in roi_ms for x in r)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
            "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

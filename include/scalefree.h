@@ -190,6 +190,18 @@ sf_status sf_get_bandwidths(const sf_index *idx, float *d_h, void *stream);
 sf_status sf_knn_neighbours(sf_index *idx, int32_t k, uint32_t *d_nbr, float *d_h, void *stream);
 
 /*
+ * sf_knn_work_counts -- the work of the kNN bandwidths (SF_BW_KNN with this k)
+ * on this index, for issue-rate accounting: one run of the same search with
+ * counters, its results discarded (the index's resident bandwidths are not
+ * touched). h_counts (host int64[3]): [0] (query, candidate) distance
+ * evaluations -- every lane of a query leaf's warp evaluates every candidate
+ * staged for the leaf, over all of the search's passes; [1] candidates staged,
+ * summed over query leaves and passes; [2] query leaves (of 32 points).
+ * Synchronises the stream. Errors: INVALID_ARG, DEGENERATE (n <= k), OOM, CUDA.
+ */
+sf_status sf_knn_work_counts(sf_index *idx, int32_t k, int64_t *h_counts, void *stream);
+
+/*
  * sf_kde_grid -- density at every node of a dims[0] x dims[1] x dims[2] grid
  * over the ROI box (Sec. 3.1, Eq. 7; Algorithm 4's output).
  *

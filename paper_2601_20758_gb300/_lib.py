@@ -83,6 +83,7 @@ _PROTOS = {
     "sf_bandwidths": (ctypes.c_int, [_vp, ctypes.POINTER(sf_params), _vp]),
     "sf_get_bandwidths": (ctypes.c_int, [_vp, _vp, _vp]),
     "sf_knn_neighbours": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "sf_knn_work_counts": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i64), _vp]),
     "sf_kde_grid": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
                                    ctypes.POINTER(sf_params), _vp, ctypes.POINTER(_dbl), _vp]),
     "sf_kde_points": (ctypes.c_int, [_vp, ctypes.POINTER(sf_box), ctypes.POINTER(_i32), _i32,
@@ -242,6 +243,13 @@ def sf_knn_neighbours(idx, k, d_nbr, d_h=None, stream=None):
     pn = _dev_buf(d_nbr, "d_nbr", "u32", n * max(int(k), 0))
     ph = None if d_h is None else _dev_buf(d_h, "d_h", "f32", n)
     _check("sf_knn_neighbours", load().sf_knn_neighbours(idx, int(k), pn, ph, _stream(stream)))
+
+
+def sf_knn_work_counts(idx, k, stream=None) -> dict:
+    """The kNN search's work: distance evaluations, staged candidates, query leaves."""
+    c = (_i64 * 3)()
+    _check("sf_knn_work_counts", load().sf_knn_work_counts(idx, int(k), c, _stream(stream)))
+    return {"evaluations": int(c[0]), "staged": int(c[1]), "query_leaves": int(c[2])}
 
 
 def sf_kde_grid(idx, roi: sf_box, dims, kernel, params, d_out, want_mass=False, stream=None):

@@ -11,6 +11,7 @@ namespace sf {
 const char *last_error_cstr();
 void clear_error();
 sf_status knn_neighbours(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_orig, cudaStream_t s);
+sf_status knn_work_counts(sf_index *idx, int k, int64_t *h_counts, cudaStream_t s);
 sf_status scatter_bandwidths(const sf_index *idx, float *d_h_orig, cudaStream_t s);
 sf_status select_points(const float *d_density, const uint32_t *d_ids, int64_t n, int64_t n_total,
                         double threshold, double percentile, uint8_t *d_mask, uint32_t *d_sel_ids,
@@ -287,6 +288,14 @@ sf_status sf_get_bandwidths(const sf_index *idx, float *d_h, void *stream) {
     if (!idx || !d_h) return fail(SF_ERR_INVALID_ARG, "sf_get_bandwidths: NULL argument");
     if (idx->bw_rule != SF_BW_KNN) return fail(SF_ERR_INVALID_ARG, "sf_get_bandwidths: no kNN bandwidths built");
     return scatter_bandwidths(idx, d_h, (cudaStream_t)stream);
+}
+
+sf_status sf_knn_work_counts(sf_index *idx, int32_t k, int64_t *h_counts, void *stream) {
+    clear_error();
+    if (!idx || !h_counts) return fail(SF_ERR_INVALID_ARG, "sf_knn_work_counts: NULL argument");
+    if (k < 1 || k > 256) return fail(SF_ERR_INVALID_ARG, "sf_knn_work_counts: k=%d outside [1, 256]", k);
+    if (idx->n <= k) return fail(SF_ERR_DEGENERATE, "sf_knn_work_counts: n <= k");
+    return knn_work_counts(idx, k, h_counts, (cudaStream_t)stream);
 }
 
 sf_status sf_knn_neighbours(sf_index *idx, int32_t k, uint32_t *d_nbr, float *d_h, void *stream) {

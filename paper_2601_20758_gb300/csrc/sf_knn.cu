@@ -60,6 +60,7 @@ struct KnnArgs {
     double *band_d;           // [slots][kBand][32] band members' FP64 d2
     uint32_t *band_i;         // [slots][kBand][32] band members' original ids
     unsigned int *next_leaf;  // work counter (zeroed before launch)
+    unsigned long long *work; // nullable: [0] candidates staged (all passes), [1] query leaves
 };
 
 __device__ __forceinline__ float d2_f32(float4 a, float4 b) {
@@ -79,7 +80,9 @@ __device__ __forceinline__ bool key_less(double da, uint32_t ia, double db, uint
 }
 
 // Per-warp candidate search: every lane holds one query point and the squared
-// radius r2 of its ball (negative: the lane takes no part).
+// radius r2 of its ball (negative: the lane takes no part). COUNT: the work
+// accounting variant (sf_knn_work_counts).
+template <bool COUNT>
 struct KnnWarp {
     const TreeView &tv;
     const uint32_t *perm;
@@ -91,6 +94,7 @@ struct KnnWarp {
     float env_lo[3], env_hi[3];  // warp envelope of all balls
     int nlist;
     bool overflow;
+    unsigned long long ncand = 0;  // COUNT only: candidates staged over all passes
 
     __device__ KnnWarp(const TreeView &t, const uint32_t *p, KnnWarpSmem &s, int *c, uint32_t *cm)
         : tv(t), perm(p), S(s), leaf_list(c), leaf_mask(cm) {}
@@ -194,6 +198,7 @@ struct KnnWarp {
             const bool in = j < tv.n && p.x >= env_lo[0] && p.x <= env_hi[0] && p.y >= env_lo[1] &&
                             p.y <= env_hi[1] && p.z >= env_lo[2] && p.z <= env_hi[2];
             const unsigned m = __ballot_sync(0xffffffffu, in);
+            if (COUNT) ncand += __popc(m);
             if (in) S.pts[__popc(m & ((1u << lane) - 1u))] = p;
             if (record >= 0 && lane == 0 && record + li < kLeafList) leaf_mask[record + li] = m;
             __syncwarp();
@@ -306,6 +311,7 @@ struct KnnWarp {
     }
 };
 
+template <bool COUNT>
 __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, uint32_t *leaf_mask, double *bd, uint32_t *bi,
                          int64_t leaf) {
     const int lane = threadIdx.x & 31;
@@ -313,7 +319,7 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, uint3
     const int k = a.k;
     const int64_t qi = leaf * kLeaf + lane;
     const bool valid = qi < tv.n;
-    KnnWarp W(tv, a.perm, S, leaf_list, leaf_mask);
+    KnnWarp<COUNT> W(tv, a.perm, S, leaf_list, leaf_mask);
     W.q = valid ? __ldg(&tv.pos[qi]) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 q = W.q;
     const uint32_t qid = valid ? __ldg(&a.perm[qi]) : 0u;
@@ -582,8 +588,13 @@ __device__ void knn_leaf(const KnnArgs &a, KnnWarpSmem &S, int *leaf_list, uint3
             for (int x = 0; x < need && x < kBand && slot + x < k; ++x)
                 a.nbr_orig[(int64_t)qid * k + slot + x] = bi[x * 32 + lane];
     }
+    if (COUNT && lane == 0) {
+        atomicAdd(&a.work[0], W.ncand);
+        atomicAdd(&a.work[1], 1ull);
+    }
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(kKnnWarps * 32, 7) k_knn(KnnArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
@@ -599,7 +610,16 @@ __global__ void __launch_bounds__(kKnnWarps * 32, 7) k_knn(KnnArgs a) {
         if ((threadIdx.x & 31) == 0) leaf = atomicAdd(a.next_leaf, 1u);
         leaf = __shfl_sync(0xffffffffu, leaf, 0);
         if ((int64_t)leaf >= nleaf) break;
-        knn_leaf(a, S, leaf_list, leaf_mask, bd, bi, (int64_t)leaf);
+        knn_leaf<COUNT>(a, S, leaf_list, leaf_mask, bd, bi, (int64_t)leaf);
+    }
+}
+
+// The kNN's work accounting: after a launch with a.work set.
+__global__ void k_knn_work_out(const unsigned long long *work, int64_t *out) {
+    if (threadIdx.x == 0) {
+        out[0] = (int64_t)work[0] * 32;  // (lane, candidate) distance evaluations
+        out[1] = (int64_t)work[0];
+        out[2] = (int64_t)work[1];
     }
 }
 
@@ -623,20 +643,23 @@ __global__ void k_scatter_f(const float *__restrict__ v, const uint32_t *__restr
         out[perm[i]] = v[i];
 }
 
-sf_status knn_run(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_sorted, cudaStream_t s) {
+sf_status knn_run(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_sorted, cudaStream_t s,
+                  unsigned long long *d_work = nullptr) {
     KnnArgs a;
     a.tv = idx->view();
     a.perm = idx->perm;
     a.k = k;
     a.h_sorted = d_h_sorted;
     a.nbr_orig = d_nbr_orig;
+    a.work = d_work;
     const size_t smem = sizeof(KnnWarpSmem) * kKnnWarps;
-    static std::atomic<uint64_t> attr{0};
-    SF_TRY_CUDA(smem_attr_once(k_knn, smem, attr));
+    auto kern = d_work ? k_knn<true> : k_knn<false>;
+    static std::atomic<uint64_t> attr_plain{0}, attr_count{0};
+    SF_TRY_CUDA(smem_attr_once(kern, smem, d_work ? attr_count : attr_plain));
     int dev = 0, sms = 0, per_sm = 0;
     SF_TRY_CUDA(cudaGetDevice(&dev));
     SF_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SF_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn, kKnnWarps * 32, smem));
+    SF_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kKnnWarps * 32, smem));
     if (per_sm < 1) per_sm = 1;
     // persistent: one resident wave, never more blocks than leaves need
     const int64_t need_blocks = (idx->cnt[0] + kKnnWarps - 1) / kKnnWarps;
@@ -649,8 +672,8 @@ sf_status knn_run(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_sorted,
     a.next_leaf = sc.get<unsigned int>(1);
     SF_TRY_SCRATCH(sc);
     SF_TRY_CUDA(cudaMemsetAsync(a.next_leaf, 0, sizeof(unsigned int), s));
-    KTimer timer("k_knn", s);
-    SF_TRY_CUDA(launch(k_knn, dim3((unsigned)blocks), dim3(kKnnWarps * 32), smem, s, a));
+    KTimer timer(d_work ? "k_knn_count" : "k_knn", s);
+    SF_TRY_CUDA(launch(kern, dim3((unsigned)blocks), dim3(kKnnWarps * 32), smem, s, a));
     return SF_OK;
 }
 
@@ -678,6 +701,23 @@ sf_status knn_neighbours(sf_index *idx, int k, uint32_t *d_nbr_orig, float *d_h_
         SF_TRY_CUDA(launch(k_scatter_f, dim3(g), dim3(256), 0, s, (const float *)h,
                            (const uint32_t *)idx->perm, idx->n, d_h_orig));
     }
+    return SF_OK;
+}
+
+// The work of one kNN run (the index's resident bandwidths are left as they are):
+// h_counts[0] (lane, candidate) distance evaluations, [1] candidates staged per
+// query leaf, summed over all passes, [2] query leaves. Synchronises the stream.
+sf_status knn_work_counts(sf_index *idx, int k, int64_t *h_counts, cudaStream_t s) {
+    Scratch sc(s);
+    float *h = sc.get<float>(idx->n);
+    unsigned long long *work = sc.get<unsigned long long>(2);
+    int64_t *out = sc.get<int64_t>(3);
+    SF_TRY_SCRATCH(sc);
+    SF_TRY_CUDA(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), s));
+    SF_TRY(knn_run(idx, k, nullptr, h, s, work));
+    SF_TRY_CUDA(launch(k_knn_work_out, dim3(1), dim3(32), 0, s, (const unsigned long long *)work, out));
+    SF_TRY_CUDA(cudaMemcpyAsync(h_counts, out, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SF_TRY_CUDA(cudaStreamSynchronize(s));
     return SF_OK;
 }
 

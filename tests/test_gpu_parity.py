@@ -433,3 +433,28 @@ def test_select_empty(L):
     mask = torch.full((10,), 3, dtype=torch.uint8, device="cuda")
     cnt, _ = L.sf_select(None, None, None, 0, 10, percentile=90.0, d_mask=mask)
     assert cnt == 0 and int(mask.sum()) == 0
+
+
+def test_knn_work_counts(L):
+    """The kNN work accounting: every lane of a query leaf evaluates every staged
+    candidate; each query leaf stages at least its own k + 1 nearest points; the
+    index's resident bandwidths are left untouched."""
+    xyz = synth.plain_cloud(20000, seed=23)
+    idx, d = _index(L, xyz)
+    try:
+        p = L.make_params(rule=L.SF_BW_KNN, k=32)
+        L.sf_bandwidths(idx, p)
+        n = xyz.shape[0]
+        h0 = torch.empty(n, device="cuda")
+        L.sf_get_bandwidths(idx, h0)
+        wc = L.sf_knn_work_counts(idx, 32)
+        h1 = torch.empty(n, device="cuda")
+        L.sf_get_bandwidths(idx, h1)
+        assert torch.equal(h0, h1)
+        assert wc["query_leaves"] == (n + 31) // 32
+        assert wc["evaluations"] == 32 * wc["staged"]
+        assert wc["staged"] >= 33 * wc["query_leaves"]
+        with pytest.raises(RuntimeError):
+            L.sf_knn_work_counts(idx, 0)
+    finally:
+        L.sf_free_index(idx)
