@@ -346,7 +346,8 @@ struct DensityCall {
 // Per-node moments of the index (sf_moments.cu), built once with the index:
 // for node g, mom[3g] = (mu_hi, M0), mom[3g+1] = (mu_lo, 0), mom[3g+2] = (C, 0)
 // with M0 the point count, mu = centroid (mu_hi + mu_lo in float pairs) and
-// C_k = sum (y_k - mu_k)^2 (FP64 sums, rounded once).
+// C_k = sum (y_k - mu_k)^2 (leaves: FP32 sums of offsets within the leaf; inner
+// nodes: FP64 parallel-axis combine of their children, rounded once).
 sf_status build_moments(sf_index *idx, cudaStream_t s);
 // Grid density by exact moments (Epanechnikov, BW_UNIFORM only); same contract
 // as density_grid. ws_bytes (nullable): return the call's bytes instead of running.

@@ -285,9 +285,9 @@ class GpuExecutor:
         from . import _lib as L
         self.L, self.torch = L, torch
         self.idx, self.kernel, self.n = idx, kernel, n_points
-        self.params = {"fp32": params, "bf16": L.make_params(rule=params.rule, k=params.k,
-                                                           scope=params.scope)}
-        self.params["bf16"].prec = L.SF_PREC_BF16
+        bf16 = L.sf_params.from_buffer_copy(params)   # every field, the precision changed
+        bf16.prec = L.SF_PREC_BF16
+        self.params = {"fp32": params, "bf16": bf16}
         self.copy_back = copy_back
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.query_stream = torch.cuda.Stream()
