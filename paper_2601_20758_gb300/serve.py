@@ -145,7 +145,9 @@ class Server:
                     self._queue.popleft()
                     self._finish(head, "rejected")   # can never fit, even alone
                     continue
-                while (self._in_flight + need > self.budget and not self._closed
+                # wait for running requests to free memory (they notify when done;
+                # need <= budget, so this ends once enough of them have finished)
+                while (self._in_flight + need > self.budget
                        and self._queue and self._queue[0] is head):
                     self._lock.wait()
                 if not self._queue or self._queue[0] is not head or not self._free_slots:
