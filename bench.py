@@ -929,6 +929,31 @@ def run_batched(args, L, torch, d_xyz, p, stream):
                        for x, y in zip(outs_b, outs_p))
         finally:
             L.sf_batch_free(plan)
+        # the same batch with the tensor-core grid variants (8-deep tiles): time, and
+        # the largest deviation from the FP32 batch relative to each ROI's peak
+        variants = {}
+        for name, prec in (("tf32", L.SF_PREC_TF32), ("bf16", L.SF_PREC_BF16)):
+            q = L.sf_params.from_buffer_copy(p)
+            q.prec = prec
+            outs_v = [torch.empty_like(o) for o in outs_p]
+            vplan = L.sf_batch_create(idx, boxes, dims, L.SF_K_GAUSS3, q, autotune.make_tune(8, ips if tz == 8 else 4),
+                                      stream)
+            try:
+                L.sf_batch_run(vplan, outs_v, stream=stream)
+                torch.cuda.synchronize()
+                ms = []
+                for _ in range(3):
+                    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    L.sf_batch_run(vplan, outs_v, stream=stream)
+                    z.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(a.elapsed_time(z))
+                vdiff = max(float(((x - y).abs().max() / y.abs().max().clamp_min(1e-30)))
+                            for x, y in zip(outs_v, outs_b))
+            finally:
+                L.sf_batch_free(vplan)
+            variants[name] = {"batched_ms": sorted(ms)[1], "max_abs_diff_vs_fp32_over_peak": vdiff}
     finally:
         L.sf_free_index(idx)
     return {"rois": len(boxes), "nodes": int(sum(d[0] * d[1] * d[2] for d in dims)),
@@ -936,7 +961,7 @@ def run_batched(args, L, torch, d_xyz, p, stream):
             "grid_edges": [int(min(d[0] for d in dims)), int(max(d[0] for d in dims))],
             "plain_ms": res["plain"], "batched_ms": res["batched"],
             "speedup": res["plain"] / res["batched"], "tile_z": tz, "items_per_warp": ips,
-            "tuning_ms": tms, "max_rel_diff_vs_plain": diff}
+            "tuning_ms": tms, "max_rel_diff_vs_plain": diff, "precision_variants": variants}
 
 
 def run_precision(L, torch, d_xyz, p, box, stream):

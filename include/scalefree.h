@@ -77,8 +77,9 @@ enum { SF_SCOPE_CLIP = 0, SF_SCOPE_GLOBAL = 1 };
  * the particles whose support covers a whole 8 x 4 x 8 node tile are summed as
  * a tensor-core product of their per-axis kernel factors in the same three
  * forms (terms off by about 1e-3 relative in TF32, 8e-3 in BF16, 2^-21 in
- * 3xTF32); the other particles stay FP32. FP32 is the default everywhere and
- * the only form of batches and of every other call. */
+ * 3xTF32); the other particles stay FP32, and so do batches (sf_batch_create)
+ * of Gaussian grids with tile_z 8. FP32 is the default everywhere and the only
+ * form of every other call. */
 enum { SF_PREC_FP32 = 0, SF_PREC_TF32 = 1, SF_PREC_3XTF32 = 2, SF_PREC_BF16 = 3 };
 
 /* Point densities: DIRECT evaluates the kernel sum at each point (self term
@@ -358,6 +359,8 @@ sf_status sf_resample_grid(const float *d_src, const sf_box *src_box, const int3
  * and, unless tune->no_graph, captures the execution into a CUDA graph that
  * sf_batch_run replays; the index must not change while a batch exists.
  * Rules KNN and FIXED, both scopes (CLIP counts N_B per ROI at creation).
+ * params->prec: FP32, or the grid variants TF32 / 3XTF32 / BF16 (Gaussian
+ * kernel, tile_z 8; see SF_PREC_*).
  *
  * rois: nroi closed boxes; dims: nroi x 3 int32 (dims[3r..3r+2] for ROI r,
  * each in [2, 4096]). d_outs: nroi device pointers, grid r of

@@ -96,7 +96,9 @@ def tune_batch(idx, boxes, dims_list, kernel, params, outs, stream=None, reps: i
             return hit["tile_z"], hit["items_per_slot"], hit.get("ms", {})
     st = torch.cuda.current_stream() if stream is None else stream
     timings = {}
-    for tz, ips in CANDIDATES:
+    # the tensor-core variants need 8-deep tiles
+    cands = CANDIDATES if getattr(params, "prec", 0) == L.SF_PREC_FP32 else [c for c in CANDIDATES if c[0] == 8]
+    for tz, ips in cands:
         plan = L.sf_batch_create(idx, boxes, dims_list, kernel, params, make_tune(tz, ips), st)
         try:
             L.sf_batch_run(plan, outs, stream=st)      # warm-up

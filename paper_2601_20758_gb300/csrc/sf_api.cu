@@ -508,14 +508,17 @@ sf_status sf_batch_create(sf_index *idx, int32_t nroi, const sf_box *rois, const
     SF_TRY(check_params(idx, params, kernel, "sf_batch_create"));
     if (params->rule == SF_BW_MBE)
         return fail(SF_ERR_INVALID_ARG, "sf_batch_create: rule MBE is per ROI; use sf_kde_grid");
-    if (params->prec != SF_PREC_FP32)
-        return fail(SF_ERR_INVALID_ARG, "sf_batch_create: grids are FP32 only");
+    if (params->prec != SF_PREC_FP32 && kernel != SF_K_GAUSS3)
+        return fail(SF_ERR_INVALID_ARG,
+                    "sf_batch_create: TF32 / 3xTF32 / BF16 grids need the Gaussian kernel");
     int tz = 8, ips = 4;
     bool graph = true;
     if (tune) {
         if (tune->tile_z != 0 && tune->tile_z != 4 && tune->tile_z != 8)
             return fail(SF_ERR_INVALID_ARG, "sf_batch_create: tile_z must be 4 or 8");
         if (tune->tile_z) tz = tune->tile_z;
+        if (tz != 8 && params->prec != SF_PREC_FP32)
+            return fail(SF_ERR_INVALID_ARG, "sf_batch_create: the tensor-core variants need tile_z 8");
         if (tune->items_per_slot < 0 || tune->items_per_slot > 64)
             return fail(SF_ERR_INVALID_ARG, "sf_batch_create: items_per_slot outside [0, 64]");
         if (tune->items_per_slot) ips = tune->items_per_slot;
@@ -546,7 +549,8 @@ sf_status sf_batch_create(sf_index *idx, int32_t nroi, const sf_box *rois, const
         }
     }
     sf::BatchPlan *plan = nullptr;
-    SF_TRY(batch_create(idx, nroi, rois, grids.data(), kernel, bw, clip, dps, tz, ips, graph, s, &plan));
+    SF_TRY(batch_create(idx, nroi, rois, grids.data(), kernel, bw, clip, dps, tz, ips, graph, s, &plan,
+                        params->prec));
     sf_batch *b = new sf_batch();
     b->plan = plan;
     b->nroi = nroi;

@@ -1749,7 +1749,7 @@ void batch_free(BatchPlan *P) {
 // rois/grids: nroi boxes and GridSpecs; dps: device DensityParams per ROI (owned by the plan)
 sf_status batch_create(sf_index *idx, int nroi, const sf_box *rois, const GridSpec *grids,
                        int kernel, int bw, bool clip, DensityParams *d_dps, int tz, int ips,
-                       bool use_graph, cudaStream_t s, BatchPlan **out) {
+                       bool use_graph, cudaStream_t s, BatchPlan **out, int prec) {
     BatchPlan *P = new BatchPlan();
     P->idx = idx;
     P->nroi = nroi;
@@ -1825,7 +1825,7 @@ sf_status batch_create(sf_index *idx, int nroi, const sf_box *rois, const GridSp
     P->a.tile_roi = (const int *)p_tr;
     P->a.ntiles = (int)ntiles;
     P->a.pairs = nullptr;
-    P->a.prec = SF_PREC_FP32;
+    P->a.prec = prec;  // the work kernel's form (tensor-core variants: Gaussian, 8-deep tiles)
     P->b.cnt = (uint32_t *)p_cnt;
     P->b.off = (uint32_t *)p_off;
     P->b.tot = (uint32_t *)p_tot;

@@ -398,7 +398,7 @@ sf_status roi_leaf_list(sf_index *idx, const sf_box &roi, Scratch &sc, int **d_l
 struct BatchPlan;
 sf_status batch_create(sf_index *idx, int nroi, const sf_box *rois, const GridSpec *grids,
                        int kernel, int bw, bool clip, DensityParams *d_dps, int tz, int ips,
-                       bool use_graph, cudaStream_t s, BatchPlan **out);
+                       bool use_graph, cudaStream_t s, BatchPlan **out, int prec = SF_PREC_FP32);
 sf_status batch_run(BatchPlan *P, float *const *outs, double *h_mass, cudaStream_t s);
 void batch_free(BatchPlan *P);
 

@@ -95,9 +95,13 @@ def test_tensor_core_rejected_where_not_defined():
         grid = torch.empty(8 ** 3, device="cuda")
         with pytest.raises(L.SFError):   # the grid variants are Gaussian only
             L.sf_kde_grid(idx, L.make_box((0, 0, 0), (1, 1, 1)), (8, 8, 8), L.SF_K_EPAN, p, grid)
-        with pytest.raises(L.SFError):   # batches are FP32 only
-            L.sf_batch_kde_grid(idx, [L.make_box((0, 0, 0), (1, 1, 1))], [(8, 8, 8)], L.SF_K_GAUSS3, p,
+        with pytest.raises(L.SFError):   # batch variants: Gaussian only
+            L.sf_batch_kde_grid(idx, [L.make_box((0, 0, 0), (1, 1, 1))], [(8, 8, 8)], L.SF_K_EPAN, p,
                                 [grid])
+        from paper_2601_20758_gb300 import autotune
+        with pytest.raises(L.SFError):   # and 8-deep tiles
+            L.sf_batch_create(idx, [L.make_box((0, 0, 0), (1, 1, 1))], [(8, 8, 8)], L.SF_K_GAUSS3, p,
+                              autotune.make_tune(4, 4))
     finally:
         L.sf_free_index(idx)
 
@@ -157,5 +161,52 @@ def test_tensor_core_grid_variants_error():
             assert rep["max_rel"] <= GRID_BOUNDS[name], (name, rep)
             assert rep["rms_rel"] <= GRID_RMS[name], (name, rep)
         assert report["3xtf32"]["max_rel"] < report["tf32"]["max_rel"] < report["bf16"]["max_rel"]
+    finally:
+        L.sf_free_index(idx)
+
+
+def test_tensor_core_grid_variants_in_batches():
+    """The grid variants in a batch (one persistent, graph-captured execution over
+    several ROIs): every ROI's grid against the FP64 oracle within the variant's
+    bounds above; a batch replays bit-identically."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_20758_gb300 import build
+    build.build()
+    from paper_2601_20758_gb300 import _lib as L
+    xyz = synth.plain_cloud(20000, seed=23)
+    rois = [((0.40, 0.42, 0.45), (0.52, 0.55, 0.56)), ((0.3, 0.35, 0.3), (0.6, 0.58, 0.62)),
+            ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0))]
+    dims = [(33, 30, 27), (20, 22, 24), (24, 24, 24)]
+    d = torch.from_numpy(xyz).cuda()
+    idx = L.sf_build_index(d)
+    try:
+        p = L.make_params(rule=L.SF_BW_KNN, k=32)
+        L.sf_bandwidths(idx, p)
+        h, _, _ = oracle.knn(xyz, 32)
+        refs = [oracle.kde_grid(xyz, oracle.iso_ell(h), r, dm, oracle.GAUSS3, oracle.SCOPE_GLOBAL)
+                for r, dm in zip(rois, dims)]
+        boxes = [L.make_box(*r) for r in rois]
+        for name, prec in (("3xtf32", L.SF_PREC_3XTF32), ("tf32", L.SF_PREC_TF32), ("bf16", L.SF_PREC_BF16)):
+            q = L.make_params(rule=L.SF_BW_KNN, k=32)
+            q.prec = prec
+            outs = [torch.empty(dm[0] * dm[1] * dm[2], device="cuda") for dm in dims]
+            plan = L.sf_batch_create(idx, boxes, dims, L.SF_K_GAUSS3, q)
+            try:
+                L.sf_batch_run(plan, outs)
+                first = [o.clone() for o in outs]
+                L.sf_batch_run(plan, outs)
+                torch.cuda.synchronize()
+                for a, b in zip(first, outs):
+                    assert torch.equal(a, b), name
+            finally:
+                L.sf_batch_free(plan)
+            for ri, (o, ref) in enumerate(zip(outs, refs)):
+                r = ref["rho"]
+                big = r >= 1e-3 * r.max()
+                g = o.cpu().numpy().astype(np.float64)
+                rel = np.maximum(np.abs(g - r) - ref["amb"], 0.0)[big] / r[big]
+                assert rel.max() <= GRID_BOUNDS[name], (name, ri, float(rel.max()))
+                assert np.sqrt(np.mean(rel ** 2)) <= GRID_RMS[name], (name, ri)
     finally:
         L.sf_free_index(idx)
