@@ -1531,7 +1531,8 @@ static RoiDesc roi_desc(const GridSpec &g, int tz, const float2 *axis, int tile_
     return r;
 }
 
-// The tile gather with TZ-deep tiles and ips work items per resident warp;
+// The tile gather with TZ-deep tiles and ips work items per resident warp (8:
+// measured equal or up to 7% faster than 4 on the zoom grids of the 1.07B cloud);
 // shallow (non-null): see mr_once (returns early, nothing written, when set).
 template <int TZ>
 static sf_status grid_gather(sf_index *idx, const sf_box &roi, const GridSpec &g,
@@ -1594,7 +1595,7 @@ static sf_status density_grid_gather(sf_index *idx, const sf_box &roi, const Gri
                                      cudaStream_t s, unsigned long long *d_pairs, StatusPeek *peek,
                                      int64_t *ws_bytes) {
     bool shallow = false;
-    SF_TRY(grid_gather<kTileZ>(idx, roi, g, call, d_out, d_mass, s, d_pairs, peek, ws_bytes, 4,
+    SF_TRY(grid_gather<kTileZ>(idx, roi, g, call, d_out, d_mass, s, d_pairs, peek, ws_bytes, 8,
                                call.prec == SF_PREC_FP32 ? &shallow : nullptr));
     if (!shallow) return SF_OK;
     if (ws_bytes) *ws_bytes = 0;
