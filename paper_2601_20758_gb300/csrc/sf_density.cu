@@ -1600,7 +1600,13 @@ static sf_status density_grid_gather(sf_index *idx, const sf_box &roi, const Gri
                                call.prec == SF_PREC_FP32 ? &shallow : nullptr));
     if (!shallow) return SF_OK;
     if (ws_bytes) *ws_bytes = 0;
-    return grid_gather<4>(idx, roi, g, call, d_out, d_mass, s, d_pairs, peek, ws_bytes, 32, nullptr);
+    const sf_status st = grid_gather<4>(idx, roi, g, call, d_out, d_mass, s, d_pairs, peek, ws_bytes,
+                                        32, nullptr);
+    if (st != SF_ERR_CAPACITY) return st;
+    // the shallow tiles' lists would pass 2^31 entries where the 8-deep ones fit: keep those
+    clear_error();
+    if (ws_bytes) *ws_bytes = 0;
+    return grid_gather<kTileZ>(idx, roi, g, call, d_out, d_mass, s, d_pairs, peek, ws_bytes, 8, nullptr);
 }
 
 // The pair-by-pair gather, or the exact moment form (sf_moments.cu) when the
